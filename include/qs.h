@@ -1,0 +1,258 @@
+/*
+ * qs.h -- C ABI of the GB300 state-vector simulator core.
+ *
+ * The library applies a compiled gate list to a 2^n-amplitude state vector
+ * held in GPU memory (full-state, Schroedinger-style simulation, Sec. II-B of
+ * arXiv 2410.09326 "QOPS"), with the paper's profile-guided optimisations:
+ * virtual swap (Sec. III-D), gate merging generalised to k-qubit fusion
+ * (Sec. III-D "Single-qubit gate merging"), and a pass activator driven by
+ * per-gate counters and per-block timings (Sec. III-A "PGO compilation flow",
+ * Sec. III-C "QOPS Profiling Library").
+ *
+ * Conventions
+ *  - Qubit q_i is bit i of the basis index (little-endian). The paper's
+ *    storage example puts q_0 in the most significant ("file") segment; this
+ *    library does not.
+ *  - Amplitudes are interleaved complex: QS_C64 = {float re, im} (8 bytes),
+ *    QS_C128 = {double re, im} (16 bytes). Gate matrices follow the OpenQASM 2
+ *    qelib1 definitions; RZ(t) = diag(e^{-it/2}, e^{it/2}).
+ *  - A state carries a logical->physical qubit map `perm` (perm[l] = the
+ *    physical bit that holds logical qubit l). Gates name logical qubits.
+ *    Amplitude a_phys[P(i)] equals the logical amplitude a[i] where
+ *    P(i) = sum_l bit_l(i) << perm[l].
+ *  - Every call returns a qs_status; on failure qs_last_error() gives a
+ *    message (thread-local, valid until the next call on that thread).
+ *    Nothing aborts the process.
+ *  - Calls that launch work are asynchronous on the state's stream, except
+ *    qs_measure_probs, qs_norm and qs_read_state, which synchronise it.
+ *  - A CUDA error seen by a call marks the state invalid; later calls on it
+ *    return QS_ESTATE.
+ */
+#ifndef QS_ABI_H_
+#define QS_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QS_OK = 0,
+  QS_EINVAL = 1,        /* bad argument (qubit out of range, duplicate, ...) */
+  QS_ENOMEM = 2,        /* device or host allocation failed */
+  QS_ECUDA = 3,         /* a CUDA call failed; the state is now invalid */
+  QS_EUNSUPPORTED = 4,  /* valid request this build does not handle */
+  QS_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
+  QS_ESTATE = 6         /* the state is invalid after an earlier CUDA error */
+} qs_status;
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/*
+ * Gate types. The paper's counter-based profiler (Sec. III-C) keeps 33 gate
+ * counters per qubit, naming H first, S second, T third, CPhase, CU1 and SWAP
+ * among them and using 0 for H and 11 for CPhase in its context records. The
+ * full list is in a missing figure, so the ids below are this library's own:
+ * H=0, S=1, T=2, CPHASE=11, CU1=12, SWAP=13 follow the text, the rest fill
+ * the gaps.
+ */
+typedef enum {
+  QS_H = 0, QS_S = 1, QS_T = 2, QS_X = 3, QS_Y = 4, QS_Z = 5, QS_SDG = 6,
+  QS_TDG = 7, QS_RX = 8, QS_RY = 9, QS_RZ = 10, QS_CPHASE = 11, QS_CU1 = 12,
+  QS_SWAP = 13, QS_CX = 14, QS_CZ = 15, QS_CY = 16, QS_CH = 17, QS_CRX = 18,
+  QS_CRY = 19, QS_CRZ = 20, QS_U1 = 21, QS_U2 = 22, QS_U3 = 23, QS_SX = 24,
+  QS_SXDG = 25, QS_ID = 26, QS_RZZ = 27, QS_RXX = 28, QS_RYY = 29,
+  QS_CCX = 30, QS_CSWAP = 31, QS_CU3 = 32,
+  QS_N_GATE_TYPES = 33
+} qs_op;
+
+#define QS_MAX_QUBITS 40   /* the paper's profiler supports 40 qubits */
+#define QS_MAX_N_C64 34    /* 2^34 * 8 B = 128 GiB of HBM */
+#define QS_MAX_N_C128 33   /* 2^33 * 16 B = 128 GiB of HBM */
+#define QS_MAX_FUSE 6      /* widest dense fused block */
+#define QS_MAX_DIAG 10     /* widest diagonal fused block (phase table 2^10) */
+
+/* One gate: q[0..nc-1] are controls, then targets (logical qubits). 32 B. */
+typedef struct {
+  uint8_t op;    /* qs_op */
+  uint8_t nq;    /* controls + targets, must match the op */
+  uint8_t q[6];
+  double p[3];   /* angles in radians; unused entries ignored */
+} qs_gate;
+
+/* Flags of qs_apply_circuit. */
+#define QS_PLAIN ((uint64_t)0)              /* one kernel per gate, SWAP moves data */
+#define QS_VSWAP ((uint64_t)1 << 0)         /* SWAPs become relabellings of perm */
+#define QS_FUSE ((uint64_t)1 << 1)          /* k-qubit fusion, k from QS_FUSE_K */
+#define QS_DIAG ((uint64_t)1 << 2)          /* diagonal runs fuse up to QS_MAX_DIAG wide */
+#define QS_TC ((uint64_t)1 << 3)            /* dense k>=4 blocks on tensor cores */
+#define QS_PROFILE ((uint64_t)1 << 4)       /* time every block with CUDA events */
+#define QS_RELOCATE ((uint64_t)1 << 5)      /* profile-guided hot-qubit relocation */
+#define QS_PGO_RULES ((uint64_t)1 << 8)     /* pick flags with the paper's counter rules */
+#define QS_PGO_MEASURED ((uint64_t)1 << 9)  /* pick flags from a measured block profile */
+#define QS_FUSE_K(k) ((uint64_t)((k) & 15) << 16)
+#define QS_FUSE_K_OF(f) ((int)(((f) >> 16) & 15))
+
+/* Tunables; pass NULL for defaults (qs_default_opts). */
+typedef struct {
+  int merge_run;        /* 1q-merge activation: longest 1q run > this (paper: e.g. five) */
+  double t_ratio;       /* rotation-folding activation: T count / gates (paper: e.g. 10%) */
+  int low_bits;         /* physical bits below this are "fast" (chunk-segment analogue) */
+  double reloc_share;   /* relocate a high qubit carrying >= this share of block time */
+  int diag_max;         /* widest diagonal block, 1..QS_MAX_DIAG */
+  int threads;          /* launch override: threads per CTA (0 = tuned default) */
+  int reserved[6];
+} qs_opts;
+
+void qs_default_opts(qs_opts *out);
+
+typedef struct qs_state qs_state;
+
+/*
+ * Allocates a state of n qubits in library-owned device memory on the
+ * current device and sets it to |0...0> with perm = identity. cuda_stream is
+ * a cudaStream_t (NULL = legacy default stream) that all work on the state is
+ * ordered on. n must be 1..QS_MAX_N_C64 (c64) or 1..QS_MAX_N_C128 (c128).
+ */
+qs_status qs_alloc_state(int n, qs_dtype dtype, void *cuda_stream, qs_state **out);
+
+/*
+ * Wraps caller-owned device memory (for example a torch tensor) of
+ * 2^n amplitudes of the given dtype, 16-byte aligned. The contents are left
+ * as they are (perm = identity); qs_free_state does not free the memory.
+ */
+qs_status qs_attach_state(void *dev_ptr, int n, qs_dtype dtype, void *cuda_stream, qs_state **out);
+
+/* Releases the handle (and the amplitudes when library-owned). NULL is a no-op. */
+void qs_free_state(qs_state *st);
+
+/* Sets the state to the logical basis state |x> and perm to identity. */
+qs_status qs_set_basis(qs_state *st, uint64_t x);
+
+/*
+ * IR ingest (the simulator's input format, Sec. III-A: the compiler emits
+ * OpenQASM). Parses the OpenQASM-2 subset "qreg q[N]; name(p..) q[a],q[b];"
+ * with the gate names of qs_op (lower case: h s t x y z sdg tdg rx ry rz cp
+ * cu1 swap cx cz cy ch crx cry crz u1 u2 u3 sx sxdg id rzz rxx ryy ccx cswap
+ * cu3). Writes up to `cap` gates; *n_gates receives the total count and
+ * *n_qubits the register size. Returns QS_EINVAL with the line number in
+ * qs_last_error on a syntax error, or when the text holds more than cap gates
+ * (*n_gates is still set, so a caller can size a buffer with cap = 0).
+ */
+qs_status qs_parse_qasm(const char *text, int *n_qubits, qs_gate *gates, size_t cap, size_t *n_gates);
+
+/*
+ * Applies gates[0..n_gates) in order. flags select the passes: QS_PLAIN runs
+ * one kernel per gate; QS_VSWAP absorbs SWAPs into perm (Sec. III-D "Virtual
+ * swap"); QS_FUSE | QS_FUSE_K(k) groups gates into dense blocks of at most k
+ * qubits, commuting gates past each other only where they act diagonally on
+ * every shared qubit; QS_DIAG lets diagonal runs grow to opts->diag_max
+ * qubits; QS_TC runs dense blocks with 4..6 targets on the tensor cores;
+ * QS_PGO_RULES / QS_PGO_MEASURED replace the pass flags by the activator's
+ * choice (see qs_pgo_select). gates is copied during the call; the launches
+ * are asynchronous on the state's stream.
+ */
+qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                           const qs_opts *opts);
+
+/*
+ * Profiling (Sec. III-C). Counter-based: every applied gate increments
+ * counters[q][op] for each logical qubit q it touches, and the longest run of
+ * consecutive one-qubit gates per qubit is kept (the activator's merge
+ * counter, Sec. III-D). Context-based: the paper records one tuple per gate
+ * (meta type 0 = one-qubit, 1 = two-qubit, 3 = SWAP; qubits; gate type;
+ * timestamp); here one record per launched block of the last apply call,
+ * with meta 4 for a fused block, its physical qubits, and -- when the call
+ * had QS_PROFILE -- its start time and device time from CUDA events.
+ */
+typedef struct {
+  int32_t index;     /* launch order within the last apply call */
+  uint8_t kind;      /* 0 dense block, 1 diagonal block, 2 physical bit exchange */
+  uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) */
+  uint8_t nctrl;     /* control bits that must be 1: only 2^(n-nctrl) amplitudes move */
+  uint8_t tc;        /* 1 if it ran on the tensor cores */
+  int8_t qubits[QS_MAX_DIAG]; /* physical qubits ascending, -1 padded */
+  uint8_t meta;      /* 0 one-qubit gate, 1 two-qubit gate, 3 swap, 4 fused block */
+  uint8_t op;        /* qs_op of a single-gate block, 255 for a fused block */
+  int32_t n_gates;   /* gates merged into the block */
+  uint64_t cmask;    /* physical control bits (the block acts where all are 1) */
+  double bytes;      /* algorithmic bytes: 2 x amplitudes changed x amplitude size */
+  double t_start_ms; /* start relative to the first block (QS_PROFILE), else -1 */
+  double ms;         /* device time (QS_PROFILE), else -1 */
+} qs_block_record;
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_blocks;           /* blocks launched by the last apply call */
+  int64_t gates_seen;         /* gates counted since the last reset */
+  int32_t gates_last;         /* gates in the last apply call */
+  int32_t swaps_absorbed;     /* SWAPs the last call turned into relabellings */
+  uint64_t flags_used;        /* flags the last call ran with (after PGO) */
+  int64_t counters[QS_MAX_QUBITS][QS_N_GATE_TYPES];
+  int32_t max_1q_run[QS_MAX_QUBITS];
+  double total_ms;            /* sum of block times of the last call, -1 if untimed */
+  double total_bytes;         /* sum of algorithmic bytes of the last call */
+  double h2d_bytes;           /* gate data the last call shipped to the device
+                                 (kernel parameters and matrix uploads) */
+} qs_profile_summary;
+
+/*
+ * Fills *out and up to cap block records of the last apply call (*n_recs gets
+ * the total). With QS_PROFILE timings this waits for the last block's event.
+ */
+qs_status qs_profile(qs_state *st, qs_profile_summary *out, qs_block_record *recs, size_t cap,
+                     size_t *n_recs);
+
+/* Clears the counters and records (start of a new profiling run). */
+qs_status qs_profile_reset(qs_state *st);
+
+/*
+ * The host passes alone (virtual swap, fusion, classification), without a
+ * GPU: the plan qs_apply_circuit would launch for a state of n qubits whose
+ * map is *perm_inout (n entries, updated for absorbed SWAPs). Fills up to cap
+ * records (ms = -1) and, when mats is not NULL, the blocks' matrices in FP64
+ * as interleaved (re, im) pairs, block after block: (2^k)^2 entries for a
+ * dense block (row-major over the block's ascending physical qubits, local
+ * index sum_j bit(q_j) << j), 2^k phases for a diagonal block, none for an
+ * exchange. *n_blocks and *mats_len (complex entries) receive the totals.
+ */
+qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, const qs_opts *opts,
+                  int8_t *perm_inout, qs_block_record *recs, size_t cap, size_t *n_blocks,
+                  double *mats, size_t mats_cap, size_t *mats_len);
+
+/* Logical->physical map: perm_out[l] = physical bit of logical qubit l (n entries). */
+qs_status qs_get_perm(const qs_state *st, int8_t *perm_out);
+
+/*
+ * Marginal probabilities of m logical qubits (FP64 accumulation on the GPU):
+ * host_out[b] = sum of |a_i|^2 over logical indices i whose bit
+ * logical_qubits[j] equals bit j of b; 2^m doubles, m in 0..min(n, 26).
+ * m = 0 gives the squared norm. Synchronises the stream.
+ */
+qs_status qs_measure_probs(qs_state *st, const int *logical_qubits, int m, double *host_out);
+
+/* Squared norm sum |a_i|^2 in FP64. Synchronises the stream. */
+qs_status qs_norm(qs_state *st, double *host_out);
+
+/*
+ * Copies the amplitudes to host memory (2^n of the state's dtype). With
+ * logical_order != 0 the state is first brought to perm = identity on the
+ * GPU by physical bit exchanges (which changes the device layout and perm);
+ * with 0 the physical layout is copied as it is. Synchronises the stream.
+ */
+qs_status qs_read_state(qs_state *st, void *host_out, int logical_order);
+
+/* Copies 2^n amplitudes from host memory into the state (physical layout). */
+qs_status qs_write_state(qs_state *st, const void *host_in);
+
+/* Device pointer of the amplitudes (for callers that share the buffer). */
+qs_status qs_device_ptr(const qs_state *st, void **out);
+
+const char *qs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_ABI_H_ */

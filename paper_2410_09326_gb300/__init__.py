@@ -1,0 +1,292 @@
+"""Python binding of the GB300 state-vector simulator core (libqs.so).
+
+Argument marshalling only: every step of the simulation (parsing, virtual
+swap, fusion, the kernels, the reductions) runs in the native library
+declared in `include/qs.h`. Function names match the C ABI. Import fails
+loudly when the library has not been built (see `build.py`); there is no
+CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_EUNSUPPORTED, QS_ETIMEOUT, QS_ESTATE = range(7)
+QS_C64, QS_C128 = 0, 1
+
+QS_PLAIN = 0
+QS_VSWAP = 1 << 0
+QS_FUSE = 1 << 1
+QS_DIAG = 1 << 2
+QS_TC = 1 << 3
+QS_PROFILE = 1 << 4
+QS_RELOCATE = 1 << 5
+QS_PGO_RULES = 1 << 8
+QS_PGO_MEASURED = 1 << 9
+
+
+def QS_FUSE_K(k):
+    return (k & 15) << 16
+
+
+QS_N_GATE_TYPES = 33
+QS_MAX_QUBITS = 40
+QS_MAX_DIAG = 10
+
+OPS = ["h", "s", "t", "x", "y", "z", "sdg", "tdg", "rx", "ry", "rz", "cp", "cu1", "swap",
+       "cx", "cz", "cy", "ch", "crx", "cry", "crz", "u1", "u2", "u3", "sx", "sxdg", "id",
+       "rzz", "rxx", "ryy", "ccx", "cswap", "cu3"]
+
+GATE_DTYPE = np.dtype([("op", "u1"), ("nq", "u1"), ("q", "u1", (6,)), ("p", "<f8", (3,))])
+assert GATE_DTYPE.itemsize == 32
+
+
+class QsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"qs status {status}: {msg}")
+        self.status = status
+
+
+class qs_opts(ctypes.Structure):
+    _fields_ = [("merge_run", ctypes.c_int), ("t_ratio", ctypes.c_double),
+                ("low_bits", ctypes.c_int), ("reloc_share", ctypes.c_double),
+                ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
+
+
+class qs_block_record(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int32), ("kind", ctypes.c_uint8), ("k", ctypes.c_uint8),
+                ("nctrl", ctypes.c_uint8), ("tc", ctypes.c_uint8),
+                ("qubits", ctypes.c_int8 * QS_MAX_DIAG), ("meta", ctypes.c_uint8),
+                ("op", ctypes.c_uint8), ("n_gates", ctypes.c_int32), ("cmask", ctypes.c_uint64),
+                ("bytes", ctypes.c_double),
+                ("t_start_ms", ctypes.c_double), ("ms", ctypes.c_double)]
+
+
+class qs_profile_summary(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("gates_seen", ctypes.c_int64), ("gates_last", ctypes.c_int32),
+                ("swaps_absorbed", ctypes.c_int32), ("flags_used", ctypes.c_uint64),
+                ("counters", (ctypes.c_int64 * QS_N_GATE_TYPES) * QS_MAX_QUBITS),
+                ("max_1q_run", ctypes.c_int32 * QS_MAX_QUBITS),
+                ("total_ms", ctypes.c_double), ("total_bytes", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_double)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Loads libqs.so; raises if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libqs.so is not built ({path}); run paper_2410_09326_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    sigs = {
+        "qs_default_opts": (None, [ctypes.POINTER(qs_opts)]),
+        "qs_alloc_state": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "qs_attach_state": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "qs_free_state": (None, [vp]),
+        "qs_set_basis": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "qs_parse_qasm": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), vp, sz,
+                                         ctypes.POINTER(sz)]),
+        "qs_apply_circuit": (ctypes.c_int, [vp, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts)]),
+        "qs_profile": (ctypes.c_int, [vp, ctypes.POINTER(qs_profile_summary),
+                                      ctypes.POINTER(qs_block_record), sz, ctypes.POINTER(sz)]),
+        "qs_profile_reset": (ctypes.c_int, [vp]),
+        "qs_get_perm": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int8)]),
+        "qs_measure_probs": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_double)]),
+        "qs_norm": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "qs_read_state": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "qs_write_state": (ctypes.c_int, [vp, vp]),
+        "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
+        "qs_last_error": (ctypes.c_char_p, []),
+        "qs_plan": (ctypes.c_int, [ctypes.c_int, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts),
+                                   ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(qs_block_record), sz,
+                                   ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_double), sz,
+                                   ctypes.POINTER(sz)]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != QS_OK:
+        raise QsError(status, _lib.qs_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def qs_default_opts():
+    o = qs_opts()
+    load().qs_default_opts(ctypes.byref(o))
+    return o
+
+
+def qs_alloc_state(n, dtype=QS_C64, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().qs_alloc_state(n, dtype, _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def qs_attach_state(dev_ptr, n, dtype=QS_C64, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().qs_attach_state(ctypes.c_void_p(dev_ptr), n, dtype, _stream_handle(stream),
+                                  ctypes.byref(h)))
+    return h
+
+
+def qs_free_state(st):
+    load().qs_free_state(st)
+
+
+def qs_set_basis(st, x):
+    _check(load().qs_set_basis(st, x))
+
+
+def qs_parse_qasm(text):
+    """Returns (n_qubits, gates) with gates a GATE_DTYPE array."""
+    lib = load()
+    raw = text.encode() if isinstance(text, str) else text
+    n = ctypes.c_int(0)
+    cnt = ctypes.c_size_t(0)
+    st = lib.qs_parse_qasm(raw, ctypes.byref(n), None, 0, ctypes.byref(cnt))
+    if st != QS_OK and cnt.value == 0:
+        _check(st)
+    gates = np.zeros(cnt.value, dtype=GATE_DTYPE)
+    _check(lib.qs_parse_qasm(raw, ctypes.byref(n), gates.ctypes.data_as(ctypes.c_void_p),
+                             cnt.value, ctypes.byref(cnt)))
+    return n.value, gates
+
+
+def qs_apply_circuit(st, gates, flags=QS_PLAIN, opts=None):
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    _check(load().qs_apply_circuit(st, gates.ctypes.data_as(ctypes.c_void_p), gates.size, flags,
+                                   ctypes.byref(opts) if opts is not None else None))
+
+
+def qs_profile(st, with_records=True):
+    """Returns (summary, list of block records)."""
+    lib = load()
+    s = qs_profile_summary()
+    n = ctypes.c_size_t(0)
+    _check(lib.qs_profile(st, ctypes.byref(s), None, 0, ctypes.byref(n)))
+    recs = []
+    if with_records and n.value:
+        arr = (qs_block_record * n.value)()
+        _check(lib.qs_profile(st, ctypes.byref(s), arr, n.value, ctypes.byref(n)))
+        recs = list(arr)
+    return s, recs
+
+
+def qs_profile_reset(st):
+    _check(load().qs_profile_reset(st))
+
+
+def qs_get_perm(st, n):
+    out = (ctypes.c_int8 * n)()
+    _check(load().qs_get_perm(st, out))
+    return np.array(list(out), dtype=np.int64)
+
+
+def qs_measure_probs(st, logical_qubits):
+    q = np.ascontiguousarray(logical_qubits, dtype=np.int32)
+    out = np.empty(1 << len(q), dtype=np.float64)
+    _check(load().qs_measure_probs(st, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(q),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def qs_norm(st):
+    out = ctypes.c_double(0)
+    _check(load().qs_norm(st, ctypes.byref(out)))
+    return out.value
+
+
+def qs_read_state(st, n, dtype=QS_C64, logical_order=False, out=None):
+    npdt = np.complex64 if dtype == QS_C64 else np.complex128
+    if out is None:
+        out = np.empty(1 << n, dtype=npdt)
+    _check(load().qs_read_state(st, out.ctypes.data_as(ctypes.c_void_p), 1 if logical_order else 0))
+    return out
+
+
+def qs_write_state(st, host):
+    host = np.ascontiguousarray(host)
+    _check(load().qs_write_state(st, host.ctypes.data_as(ctypes.c_void_p)))
+
+
+def qs_device_ptr(st):
+    p = ctypes.c_void_p()
+    _check(load().qs_device_ptr(st, ctypes.byref(p)))
+    return p.value
+
+
+def qs_plan(n, gates, flags=QS_PLAIN, opts=None, perm=None):
+    """Host passes only. Returns (records, matrices, perm): matrices[i] is the
+    block's complex128 matrix ((2^k, 2^k) dense, (2^k,) diagonal, None exchange)."""
+    lib = load()
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    pm = (ctypes.c_int8 * n)(*(range(n) if perm is None else [int(x) for x in perm]))
+    nb = ctypes.c_size_t(0)
+    ml = ctypes.c_size_t(0)
+    args = lambda recs, cap, mats, mcap: (n, gates.ctypes.data_as(ctypes.c_void_p), gates.size, flags,
+                                          ctypes.byref(opts) if opts is not None else None, pm, recs,
+                                          cap, ctypes.byref(nb), mats, mcap, ctypes.byref(ml))
+    perm0 = (ctypes.c_int8 * n)(*pm)
+    _check(lib.qs_plan(*args(None, 0, None, 0)))
+    ctypes.memmove(pm, perm0, n)
+    recs = (qs_block_record * max(1, nb.value))()
+    mats = np.zeros(2 * max(1, ml.value), dtype=np.float64)
+    _check(lib.qs_plan(*args(recs, nb.value, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             ml.value)))
+    cm = mats.view(np.complex128)
+    out, off = [], 0
+    for r in list(recs)[: nb.value]:
+        if r.kind == 0:
+            d = 1 << r.k
+            out.append(cm[off: off + d * d].reshape(d, d).copy())
+            off += d * d
+        elif r.kind == 1:
+            d = 1 << r.k
+            out.append(cm[off: off + d].copy())
+            off += d
+        else:
+            out.append(None)
+    return list(recs)[: nb.value], out, np.array(list(pm), dtype=np.int64)
+
+
+def gates_to_array(gates):
+    """(name, qubits, params) tuples -> GATE_DTYPE array (no parsing of text)."""
+    arr = np.zeros(len(gates), dtype=GATE_DTYPE)
+    for i, g in enumerate(gates):
+        name, qs = g[0], g[1]
+        ps = g[2] if len(g) > 2 else ()
+        arr[i]["op"] = OPS.index(name)
+        arr[i]["nq"] = len(qs)
+        arr[i]["q"][: len(qs)] = qs
+        arr[i]["p"][: len(ps)] = ps
+    return arr

@@ -1,0 +1,541 @@
+// C ABI of the simulator core: state handles, the apply pipeline (ingest
+// counters -> virtual swap -> fusion -> launches), profiling and reductions.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+std::string &last_error_ref() {
+  static thread_local std::string msg;
+  return msg;
+}
+
+}  // namespace qs
+
+using namespace qs;
+
+struct qs_state {
+  int n = 0;
+  qs_dtype dtype = QS_C64;
+  void *amps = nullptr;
+  bool owned = false;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int8_t perm[QS_MAX_QUBITS] = {0};
+  bool bad = false;
+  // device scratch for reductions and wide matrices, grown on demand
+  double *d_partial = nullptr;
+  size_t partial_cap = 0;
+  double *d_out = nullptr;
+  size_t out_cap = 0;
+  void *d_mats = nullptr;
+  size_t mats_cap = 0;
+  void *h_mats = nullptr;  // pinned staging for d_mats
+  size_t h_mats_cap = 0;
+  cudaEvent_t mats_copied = nullptr;
+  // profiling (Sec. III-C): counters per logical qubit and gate type, the
+  // longest run of consecutive one-qubit gates per qubit, per-block records
+  int64_t counters[QS_MAX_QUBITS][QS_N_GATE_TYPES] = {{0}};
+  int32_t run_1q[QS_MAX_QUBITS] = {0};
+  int32_t max_run_1q[QS_MAX_QUBITS] = {0};
+  int64_t gates_seen = 0;
+  std::vector<cudaEvent_t> events;
+  std::vector<qs_block_record> recs;
+  bool recs_timed = false;
+  bool recs_resolved = false;
+  uint64_t flags_used = 0;
+  PlanStats last_stats;
+  double h2d_bytes = 0;
+};
+
+namespace {
+
+int amp_bytes(const qs_state *st) { return st->dtype == QS_C128 ? 16 : 8; }
+
+qs_status fail(qs_status s, const std::string &msg) {
+  last_error_ref() = msg;
+  return s;
+}
+
+qs_status cuda_fail(qs_state *st, cudaError_t e, const char *where) {
+  if (st) st->bad = true;
+  return fail(QS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+qs_status check_state(const qs_state *st) {
+  if (!st) return fail(QS_EINVAL, "null state");
+  if (st->bad) return fail(QS_ESTATE, "state invalid after an earlier CUDA error");
+  return QS_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T> cudaError_t grow(T *&ptr, size_t &cap, size_t need) {
+  if (need <= cap) return cudaSuccess;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  cap = 0;
+  cudaError_t e = cudaMalloc((void **)&ptr, need * sizeof(T));
+  if (e == cudaSuccess) cap = need;
+  return e;
+}
+
+qs_status make_state(int n, qs_dtype dtype, void *stream, qs_state **out) {
+  if (!out) return fail(QS_EINVAL, "null output handle");
+  *out = nullptr;
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  const int nmax = dtype == QS_C64 ? QS_MAX_N_C64 : QS_MAX_N_C128;
+  if (n < 1 || n > nmax) return fail(QS_EUNSUPPORTED, "qubit count out of range for this dtype");
+  qs_state *st = new (std::nothrow) qs_state();
+  if (!st) return fail(QS_ENOMEM, "host allocation failed");
+  st->n = n;
+  st->dtype = dtype;
+  st->stream = (cudaStream_t)stream;
+  cudaGetDevice(&st->device);
+  for (int q = 0; q < n; q++) st->perm[q] = (int8_t)q;
+  *out = st;
+  return QS_OK;
+}
+
+void record_counters(qs_state *st, const qs_gate *gates, size_t n_gates) {
+  for (size_t i = 0; i < n_gates; i++) {
+    const qs_gate &g = gates[i];
+    for (int j = 0; j < g.nq; j++) st->counters[g.q[j]][g.op]++;
+    if (g.nq == 1) {
+      int q = g.q[0];
+      st->run_1q[q]++;
+      st->max_run_1q[q] = std::max(st->max_run_1q[q], st->run_1q[q]);
+    } else {
+      for (int j = 0; j < g.nq; j++) st->run_1q[g.q[j]] = 0;
+    }
+  }
+  st->gates_seen += (int64_t)n_gates;
+}
+
+// Rule-based activator (Sec. III-A "PGO compilation flow", Sec. III-D):
+// one decision per optimisation from the counters of the circuit at hand.
+uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts &o, uint64_t base) {
+  int run[QS_MAX_QUBITS] = {0}, max_run = 0;
+  int64_t swaps = 0, two_q_low = 0, t_count = 0, dense = 0;
+  for (size_t i = 0; i < n_gates; i++) {
+    const qs_gate &g = gates[i];
+    if (g.op == QS_SWAP) swaps++;
+    if (g.op == QS_T || g.op == QS_TDG) t_count++;
+    if (!op_info(g.op).diagonal) dense++;
+    if (g.nq == 1) {
+      max_run = std::max(max_run, ++run[g.q[0]]);
+    } else {
+      for (int j = 0; j < g.nq; j++) run[g.q[j]] = 0;
+      if ((g.op == QS_CX || g.op == QS_CPHASE || g.op == QS_CU1 || g.op == QS_CZ) &&
+          (g.q[g.nq - 1] < o.low_bits))
+        two_q_low++;
+    }
+  }
+  (void)n;
+  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | (15ull << 16));
+  // virtual swap: SWAP gates present, or two-qubit gates hitting the fast
+  // segment (the paper's CPhase/CNOT counter rule)
+  if (swaps > 0 || two_q_low > 0) f |= QS_VSWAP;
+  // merging: a run of consecutive one-qubit gates above the threshold, or
+  // (GPU reading) any circuit with more than one gate, since each fused gate
+  // saves a full pass over the state
+  if (max_run > o.merge_run || n_gates > 1) f |= QS_FUSE | QS_FUSE_K(4) | QS_DIAG;
+  (void)t_count;
+  (void)dense;
+  return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+void qs_default_opts(qs_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->merge_run = 5;
+  o->t_ratio = 0.10;
+  o->low_bits = 5;
+  o->reloc_share = 0.25;
+  o->diag_max = QS_MAX_DIAG;
+  o->threads = 0;
+}
+
+const char *qs_last_error(void) { return last_error_ref().c_str(); }
+
+qs_status qs_alloc_state(int n, qs_dtype dtype, void *cuda_stream, qs_state **out) {
+  qs_status s = make_state(n, dtype, cuda_stream, out);
+  if (s != QS_OK) return s;
+  qs_state *st = *out;
+  const size_t bytes = (size_t)amp_bytes(st) << n;
+  cudaError_t e = cudaMalloc(&st->amps, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete st;
+    *out = nullptr;
+    return fail(QS_ENOMEM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+  }
+  st->owned = true;
+  e = launch_set_basis(st->amps, n, dtype == QS_C128, 0, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "qs_alloc_state");
+  return QS_OK;
+}
+
+qs_status qs_attach_state(void *dev_ptr, int n, qs_dtype dtype, void *cuda_stream, qs_state **out) {
+  if (!dev_ptr) return fail(QS_EINVAL, "null device pointer");
+  if (((uintptr_t)dev_ptr & 15) != 0) return fail(QS_EINVAL, "device pointer not 16-byte aligned");
+  qs_status s = make_state(n, dtype, cuda_stream, out);
+  if (s != QS_OK) return s;
+  (*out)->amps = dev_ptr;
+  (*out)->owned = false;
+  return QS_OK;
+}
+
+void qs_free_state(qs_state *st) {
+  if (!st) return;
+  DeviceGuard g(st->device);
+  if (st->stream) cudaStreamSynchronize(st->stream);
+  else cudaDeviceSynchronize();
+  if (st->owned && st->amps) cudaFree(st->amps);
+  if (st->d_partial) cudaFree(st->d_partial);
+  if (st->d_out) cudaFree(st->d_out);
+  if (st->d_mats) cudaFree(st->d_mats);
+  if (st->h_mats) cudaFreeHost(st->h_mats);
+  if (st->mats_copied) cudaEventDestroy(st->mats_copied);
+  for (cudaEvent_t e : st->events) cudaEventDestroy(e);
+  delete st;
+}
+
+qs_status qs_set_basis(qs_state *st, uint64_t x) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (st->n < 64 && (x >> st->n) != 0) return fail(QS_EINVAL, "basis index out of range");
+  DeviceGuard g(st->device);
+  for (int q = 0; q < st->n; q++) st->perm[q] = (int8_t)q;
+  cudaError_t e = launch_set_basis(st->amps, st->n, st->dtype == QS_C128, x, st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "qs_set_basis");
+  return QS_OK;
+}
+
+qs_status qs_get_perm(const qs_state *st, int8_t *perm_out) {
+  if (!st || !perm_out) return fail(QS_EINVAL, "null argument");
+  std::memcpy(perm_out, st->perm, st->n);
+  return QS_OK;
+}
+
+qs_status qs_device_ptr(const qs_state *st, void **out) {
+  if (!st || !out) return fail(QS_EINVAL, "null argument");
+  *out = st->amps;
+  return QS_OK;
+}
+
+qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                           const qs_opts *opts) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (n_gates && !gates) return fail(QS_EINVAL, "null gate list");
+  qs_opts o;
+  if (opts) o = *opts;
+  else qs_default_opts(&o);
+  DeviceGuard dg(st->device);
+  if (flags & QS_PGO_RULES) flags = rules_select(st->n, gates, n_gates, o, flags);
+
+  std::vector<Block> plan;
+  PlanStats stats;
+  std::string err;
+  int8_t perm[QS_MAX_QUBITS];
+  std::memcpy(perm, st->perm, sizeof(perm));
+  s = build_plan(st->n, gates, n_gates, flags, o, perm, plan, stats, err);
+  if (s != QS_OK) return fail(s, "qs_apply_circuit: " + err);
+  record_counters(st, gates, n_gates);
+
+  const bool c128 = st->dtype == QS_C128;
+  const int ab = amp_bytes(st);
+  // matrices of wide dense blocks: one pinned staging buffer, one copy
+  size_t mat_bytes = 0;
+  std::vector<size_t> mat_off(plan.size(), (size_t)-1);
+  for (size_t i = 0; i < plan.size(); i++)
+    if (block_needs_dev_matrix(plan[i], c128)) {
+      mat_off[i] = mat_bytes;
+      mat_bytes += plan[i].mat.size() * (size_t)ab;
+    }
+  cudaError_t e;
+  if (mat_bytes) {
+    if (st->mats_copied) {
+      e = cudaEventSynchronize(st->mats_copied);  // staging buffer free again
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+    } else {
+      e = cudaEventCreateWithFlags(&st->mats_copied, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+    }
+    if (mat_bytes > st->h_mats_cap) {
+      if (st->h_mats) cudaFreeHost(st->h_mats);
+      st->h_mats = nullptr;
+      st->h_mats_cap = 0;
+      e = cudaMallocHost(&st->h_mats, mat_bytes);
+      if (e != cudaSuccess) return fail(QS_ENOMEM, "pinned staging allocation failed");
+      st->h_mats_cap = mat_bytes;
+    }
+    size_t cap_bytes = st->mats_cap;
+    unsigned char *dm = (unsigned char *)st->d_mats;
+    if (mat_bytes > cap_bytes) {
+      if (dm) cudaFree(dm);
+      dm = nullptr;
+      st->mats_cap = 0;
+      e = cudaMalloc((void **)&dm, mat_bytes);
+      if (e != cudaSuccess) return fail(QS_ENOMEM, "matrix buffer allocation failed");
+      st->d_mats = dm;
+      st->mats_cap = mat_bytes;
+    }
+    for (size_t i = 0; i < plan.size(); i++) {
+      if (mat_off[i] == (size_t)-1) continue;
+      unsigned char *h = (unsigned char *)st->h_mats + mat_off[i];
+      for (size_t k = 0; k < plan[i].mat.size(); k++) {
+        if (c128) {
+          double v[2] = {plan[i].mat[k].real(), plan[i].mat[k].imag()};
+          std::memcpy(h + k * 16, v, 16);
+        } else {
+          float v[2] = {(float)plan[i].mat[k].real(), (float)plan[i].mat[k].imag()};
+          std::memcpy(h + k * 8, v, 8);
+        }
+      }
+    }
+    e = cudaMemcpyAsync(st->d_mats, st->h_mats, mat_bytes, cudaMemcpyHostToDevice, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+    e = cudaEventRecord(st->mats_copied, st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+  }
+
+  const bool prof = flags & QS_PROFILE;
+  if (prof) {
+    while (st->events.size() < plan.size() + 1) {
+      cudaEvent_t ev;
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+      st->events.push_back(ev);
+    }
+    e = cudaEventRecord(st->events[0], st->stream);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+  }
+  st->recs.clear();
+  st->recs.reserve(plan.size());
+  st->h2d_bytes = 0;
+  for (size_t i = 0; i < plan.size(); i++) {
+    const Block &b = plan[i];
+    const void *dm = mat_off[i] == (size_t)-1 ? nullptr : (const unsigned char *)st->d_mats + mat_off[i];
+    e = launch_block_with_matrix(st->amps, st->n, c128, b, dm, st->stream, o.threads);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit launch");
+    if (prof) {
+      e = cudaEventRecord(st->events[i + 1], st->stream);
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
+    }
+    qs_block_record r;
+    std::memset(&r, 0, sizeof(r));
+    r.index = (int32_t)i;
+    r.kind = (uint8_t)b.kind;
+    r.k = (uint8_t)b.k;
+    r.nctrl = (uint8_t)b.nctrl;
+    r.tc = b.tc ? 1 : 0;
+    for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
+    r.meta = (uint8_t)b.meta;
+    r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
+    r.n_gates = b.n_gates;
+      r.cmask = b.cmask;
+    r.bytes = block_bytes(b, st->n, ab);
+    st->h2d_bytes += (double)block_param_bytes(b, c128);
+    r.t_start_ms = -1;
+    r.ms = -1;
+    st->recs.push_back(r);
+  }
+  std::memcpy(st->perm, perm, sizeof(perm));
+  st->recs_timed = prof;
+  st->recs_resolved = false;
+  st->flags_used = flags;
+  st->last_stats = stats;
+  return QS_OK;
+}
+
+qs_status qs_profile(qs_state *st, qs_profile_summary *out, qs_block_record *recs, size_t cap,
+                     size_t *n_recs) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!out) return fail(QS_EINVAL, "null summary");
+  DeviceGuard dg(st->device);
+  if (st->recs_timed && !st->recs_resolved && !st->recs.empty()) {
+    cudaError_t e = cudaEventSynchronize(st->events[st->recs.size()]);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_profile");
+    for (size_t i = 0; i < st->recs.size(); i++) {
+      float a = 0, b = 0;
+      e = cudaEventElapsedTime(&a, st->events[0], st->events[i]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, st->events[i], st->events[i + 1]);
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_profile");
+      st->recs[i].t_start_ms = a;
+      st->recs[i].ms = b;
+    }
+    st->recs_resolved = true;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->n_qubits = st->n;
+  out->n_blocks = (int)st->recs.size();
+  out->gates_seen = st->gates_seen;
+  out->flags_used = st->flags_used;
+  out->swaps_absorbed = st->last_stats.swaps_absorbed;
+  out->gates_last = st->last_stats.gates_in;
+  std::memcpy(out->counters, st->counters, sizeof(st->counters));
+  std::memcpy(out->max_1q_run, st->max_run_1q, sizeof(st->max_run_1q));
+  double tot_ms = 0, tot_b = 0;
+  for (const auto &r : st->recs) {
+    tot_b += r.bytes;
+    if (r.ms >= 0) tot_ms += r.ms;
+  }
+  out->total_ms = st->recs_timed ? tot_ms : -1;
+  out->total_bytes = tot_b;
+  out->h2d_bytes = st->h2d_bytes;
+  if (n_recs) *n_recs = st->recs.size();
+  if (recs) {
+    size_t k = std::min(cap, st->recs.size());
+    std::memcpy(recs, st->recs.data(), k * sizeof(qs_block_record));
+  }
+  return QS_OK;
+}
+
+qs_status qs_profile_reset(qs_state *st) {
+  if (!st) return fail(QS_EINVAL, "null state");
+  std::memset(st->counters, 0, sizeof(st->counters));
+  std::memset(st->run_1q, 0, sizeof(st->run_1q));
+  std::memset(st->max_run_1q, 0, sizeof(st->max_run_1q));
+  st->gates_seen = 0;
+  st->recs.clear();
+  return QS_OK;
+}
+
+qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, const qs_opts *opts,
+                  int8_t *perm_inout, qs_block_record *recs, size_t cap, size_t *n_blocks, double *mats,
+                  size_t mats_cap, size_t *mats_len) {
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qubit count out of range");
+  if (!perm_inout || (n_gates && !gates)) return fail(QS_EINVAL, "null argument");
+  qs_opts o;
+  if (opts) o = *opts;
+  else qs_default_opts(&o);
+  if (flags & QS_PGO_RULES) flags = rules_select(n, gates, n_gates, o, flags);
+  std::vector<Block> plan;
+  PlanStats stats;
+  std::string err;
+  int8_t perm[QS_MAX_QUBITS];
+  std::memcpy(perm, perm_inout, n);
+  qs_status s = build_plan(n, gates, n_gates, flags, o, perm, plan, stats, err);
+  if (s != QS_OK) return fail(s, "qs_plan: " + err);
+  std::memcpy(perm_inout, perm, n);
+  size_t mlen = 0;
+  for (size_t i = 0; i < plan.size(); i++) {
+    const Block &b = plan[i];
+    if (recs && i < cap) {
+      qs_block_record r;
+      std::memset(&r, 0, sizeof(r));
+      r.index = (int32_t)i;
+      r.kind = (uint8_t)b.kind;
+      r.k = (uint8_t)b.k;
+      r.nctrl = (uint8_t)b.nctrl;
+      r.tc = b.tc ? 1 : 0;
+      for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
+      r.meta = (uint8_t)b.meta;
+      r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
+      r.n_gates = b.n_gates;
+      r.cmask = b.cmask;
+      r.bytes = block_bytes(b, n, 8);
+      r.t_start_ms = -1;
+      r.ms = -1;
+      recs[i] = r;
+    }
+    for (const cd &z : b.mat) {
+      if (mats && mlen < mats_cap) {
+        mats[2 * mlen] = z.real();
+        mats[2 * mlen + 1] = z.imag();
+      }
+      mlen++;
+    }
+  }
+  if (n_blocks) *n_blocks = plan.size();
+  if (mats_len) *mats_len = mlen;
+  return QS_OK;
+}
+
+qs_status qs_measure_probs(qs_state *st, const int *logical_qubits, int m, double *host_out) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!host_out || (m > 0 && !logical_qubits)) return fail(QS_EINVAL, "null argument");
+  if (m < 0 || m > st->n || m > 26) return fail(QS_EINVAL, "m out of range");
+  int pos[32];
+  for (int j = 0; j < m; j++) {
+    int l = logical_qubits[j];
+    if (l < 0 || l >= st->n) return fail(QS_EINVAL, "qubit out of range");
+    for (int i = 0; i < j; i++)
+      if (logical_qubits[i] == l) return fail(QS_EINVAL, "duplicate qubit");
+    pos[j] = st->perm[l];
+  }
+  DeviceGuard dg(st->device);
+  const size_t nb = (size_t)1 << m;
+  cudaError_t e = grow(st->d_partial, st->partial_cap, std::max<size_t>(1, probs_scratch_doubles(st->n, m)));
+  if (e == cudaSuccess) e = grow(st->d_out, st->out_cap, nb);
+  if (e != cudaSuccess) return fail(QS_ENOMEM, "scratch allocation failed");
+  e = launch_probs(st->amps, st->n, st->dtype == QS_C128, pos, m, st->d_partial, st->d_out, st->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, st->d_out, nb * sizeof(double), cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "qs_measure_probs");
+  return QS_OK;
+}
+
+qs_status qs_norm(qs_state *st, double *host_out) { return qs_measure_probs(st, nullptr, 0, host_out); }
+
+qs_status qs_read_state(qs_state *st, void *host_out, int logical_order) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!host_out) return fail(QS_EINVAL, "null argument");
+  DeviceGuard dg(st->device);
+  cudaError_t e = cudaSuccess;
+  if (logical_order) {
+    // undo the relabelling with physical bit exchanges, one per cycle step
+    for (int l = 0; l < st->n; l++) {
+      if (st->perm[l] == l) continue;
+      int other = -1;
+      for (int k = 0; k < st->n; k++)
+        if (st->perm[k] == l) other = k;
+      e = launch_permute(st->amps, st->n, st->dtype == QS_C128, st->perm[l], l, st->stream);
+      if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
+      st->perm[other] = st->perm[l];
+      st->perm[l] = (int8_t)l;
+    }
+  }
+  e = cudaMemcpyAsync(host_out, st->amps, (size_t)amp_bytes(st) << st->n, cudaMemcpyDeviceToHost, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
+  return QS_OK;
+}
+
+qs_status qs_write_state(qs_state *st, const void *host_in) {
+  qs_status s = check_state(st);
+  if (s != QS_OK) return s;
+  if (!host_in) return fail(QS_EINVAL, "null argument");
+  DeviceGuard dg(st->device);
+  cudaError_t e = cudaMemcpyAsync(st->amps, host_in, (size_t)amp_bytes(st) << st->n, cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(st, e, "qs_write_state");
+  return QS_OK;
+}
+
+}  // extern "C"

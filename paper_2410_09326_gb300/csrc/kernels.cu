@@ -1,0 +1,300 @@
+// CUDA kernels of the simulator core (sm_103a).
+//
+// Every kernel is one HBM pass over the amplitudes a block changes:
+//  - k_dense_param / k_dense_smem: a fused block with K targets (the 2^K x 2^K
+//    product matrix of Sec. III-D's merged gates). One thread owns one group
+//    of 2^K amplitudes at a time; consecutive threads own groups whose bases
+//    differ in the lowest free bits, so a warp's loads for one matrix column
+//    are contiguous whenever the targets sit above bit 4. The matrix of
+//    blocks with K <= 5 (c64) / K <= 4 (c128) travels in the kernel's
+//    parameter space, so the fully unrolled mat-vec reads its entries as
+//    constant-bank operands of the FMAs and costs no loads.
+//  - k_diag: a diagonal block of up to QS_MAX_DIAG qubits: one multiply by a
+//    phase looked up in shared memory.
+//  - k_permute: exchange of two physical bits (a plain SWAP, Sec. III-D; also
+//    used to restore logical order).
+//  - k_probs / k_probs_reduce: FP64 marginal probabilities (Sec. II-B, "final
+//    probability distribution") with per-CTA shared-memory histograms and a
+//    fixed-order cross-CTA sum.
+// Control bits never enter the index space: only the 2^(n - controls)
+// amplitudes whose control bits are 1 are read and written.
+#include <cstring>
+
+#include "kernels_common.cuh"
+
+namespace qs {
+namespace kern {
+
+int grid_for(long long work, int threads) {
+  const DevInfo &di = dev_info();
+  long long want = (work + threads - 1) / threads;
+  long long cap = (long long)di.sms * (di.max_threads_per_sm / threads) * 4;
+  if (cap < 1) cap = 1;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+template <typename T> struct DiagParam {
+  T tab[1 << QS_MAX_DIAG];
+  long long n_amps;  // 2^(n - controls)
+  unsigned long long cmask;
+  int nf;
+  int fixed[kMaxFixed];  // control positions ascending
+  int k;
+  int tq[QS_MAX_DIAG];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag(T *__restrict__ a, const __grid_constant__ DiagParam<T> p) {
+  using R = typename Real<T>::type;
+  __shared__ T tab[1 << QS_MAX_DIAG];
+  const int tn = 1 << p.k;
+  for (int i = threadIdx.x; i < tn; i += blockDim.x) tab[i] = p.tab[i];
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < p.n_amps; j += stride) {
+    const uint64_t idx = insert_zeros((uint64_t)j, p.fixed, p.nf) | p.cmask;
+    int l = 0;
+    for (int b = 0; b < p.k; b++) l |= (int)((idx >> p.tq[b]) & 1) << b;
+    const T w = tab[l];
+    const T v = a[idx];
+    T y;
+    y.x = fma((R)w.x, v.x, -(R)w.y * v.y);
+    y.y = fma((R)w.x, v.y, (R)w.y * v.x);
+    a[idx] = y;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_permute(T *__restrict__ a, long long n_pairs, int qa, int qb) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int fixed[2] = {qa, qb};
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n_pairs; j += stride) {
+    const uint64_t base = insert_zeros((uint64_t)j, fixed, 2);
+    const uint64_t i0 = base | (1ull << qa), i1 = base | (1ull << qb);
+    const T x = a[i0], y = a[i1];
+    a[i0] = y;
+    a[i1] = x;
+  }
+}
+
+template <typename T> __global__ void k_set_one(T *a, uint64_t idx) {
+  T one;
+  one.x = 1;
+  one.y = 0;
+  a[idx] = one;
+}
+
+constexpr int kProbsSmemBits = 12;  // shared histogram up to 4096 bins
+constexpr int kMaxProbBits = 26;
+
+struct ProbsParam {
+  long long n_amps;
+  int m;
+  int pos[kMaxProbBits];
+};
+
+__device__ __forceinline__ int extract_bits(uint64_t i, const int *pos, int m) {
+  int b = 0;
+  for (int j = 0; j < m; j++) b |= (int)((i >> pos[j]) & 1) << j;
+  return b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_probs(const T *__restrict__ a, const __grid_constant__ ProbsParam p,
+                                               double *__restrict__ partial) {
+  extern __shared__ double hist[];
+  const int nb = 1 << p.m;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0.0;
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // every lane runs the same trip count so the warp collectives stay converged
+  const long long trips = (p.n_amps + stride - 1) / stride;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long t = 0; t < trips; t++, i += stride) {
+    double v = 0.0;
+    int b = 0;
+    if (i < p.n_amps) {
+      const T x = a[i];
+      v = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+      b = extract_bits((uint64_t)i, p.pos, p.m);
+    }
+    const int b0 = __shfl_sync(0xffffffffu, b, 0);
+    if (__all_sync(0xffffffffu, b == b0)) {
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && v != 0.0) atomicAdd(&hist[b0], v);
+    } else if (v != 0.0) {
+      atomicAdd(&hist[b], v);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) partial[(size_t)blockIdx.x * nb + k] = hist[k];
+}
+
+__global__ void k_probs_reduce(const double *__restrict__ partial, int nblocks, int nb,
+                               double *__restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nb) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; b++) s += partial[(size_t)b * nb + k];
+  out[k] = s;
+}
+
+// Wide histograms: one thread per bin, looping over the summed-out bits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_probs_wide(const T *__restrict__ a, const __grid_constant__ ProbsParam p,
+                                                    int n, double *__restrict__ out) {
+  const long long nb = 1ll << p.m;
+  const long long per = 1ll << (n - p.m);
+  int rest[64];
+  int nr = 0;
+  for (int q = 0; q < n; q++) {
+    bool used = false;
+    for (int j = 0; j < p.m; j++) used |= (p.pos[j] == q);
+    if (!used) rest[nr++] = q;
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+    uint64_t base = 0;
+    for (int j = 0; j < p.m; j++) base |= (uint64_t)((b >> j) & 1) << p.pos[j];
+    double s = 0.0;
+    for (long long r = 0; r < per; r++) {
+      uint64_t idx = base;
+      for (int j = 0; j < nr; j++) idx |= (uint64_t)((r >> j) & 1) << rest[j];
+      const T x = a[idx];
+      s += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    }
+    out[b] = s;
+  }
+}
+
+template <typename T>
+cudaError_t run_block(T *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads) {
+  if (b.kind == BK_PERMUTE) {
+    k_permute<T><<<grid_for(1ll << (n - 2), threads), threads, 0, s>>>(a, 1ll << (n - 2), b.q[0], b.q[1]);
+    return cudaGetLastError();
+  }
+  if (b.kind == BK_DIAG) {
+    static thread_local DiagParam<T> p;
+    const int tn = 1 << b.k;
+    for (int i = 0; i < tn; i++) p.tab[i] = to_dev<T>(b.mat[i]);
+    p.n_amps = 1ll << (n - b.nctrl);
+    p.cmask = b.cmask;
+    fill_fixed(b, p.fixed, p.nf);
+    p.k = b.k;
+    for (int j = 0; j < b.k; j++) p.tq[j] = b.q[j];
+    k_diag<T><<<grid_for(p.n_amps, threads), threads, 0, s>>>(a, p);
+    return cudaGetLastError();
+  }
+  if constexpr (sizeof(T) == 8) return run_dense_c64((float2 *)a, n, b, dev_mat, s, threads);
+  else return run_dense_c128((double2 *)a, n, b, dev_mat, s, threads);
+}
+
+}  // namespace kern
+
+using namespace kern;
+
+const DevInfo &dev_info() {
+  static thread_local DevInfo di;
+  static thread_local int dev_cached = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev != dev_cached) {
+    cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&di.max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (di.sms <= 0) di.sms = 1;
+    if (di.max_threads_per_sm <= 0) di.max_threads_per_sm = 1024;
+    dev_cached = dev;
+  }
+  return di;
+}
+
+bool block_needs_dev_matrix(const Block &b, bool c128) {
+  return b.kind == BK_DENSE && (b.k == 6 || (c128 && b.k == 5));
+}
+
+cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
+                                     cudaStream_t s, int threads) {
+  if (threads <= 0) threads = 256;
+  if (c128) return run_block<double2>((double2 *)amps, n, b, dev_mat, s, threads);
+  return run_block<float2>((float2 *)amps, n, b, dev_mat, s, threads);
+}
+
+cudaError_t launch_block(void *amps, int n, bool c128, const Block &b, cudaStream_t s, int threads) {
+  return launch_block_with_matrix(amps, n, c128, b, nullptr, s, threads);
+}
+
+template <typename T> size_t param_bytes_t(const Block &b) {
+  if (b.kind == BK_PERMUTE) return sizeof(T *) + sizeof(long long) + 2 * sizeof(int);
+  if (b.kind == BK_DIAG) return sizeof(T *) + sizeof(DiagParam<T>);
+  switch (b.k) {
+    case 1: return sizeof(T *) + sizeof(DenseParam<T, 1>);
+    case 2: return sizeof(T *) + sizeof(DenseParam<T, 2>);
+    case 3: return sizeof(T *) + sizeof(DenseParam<T, 3>);
+    case 4: return sizeof(T *) + sizeof(DenseParam<T, 4>);
+    case 5:
+      if (sizeof(T) == 8) return sizeof(T *) + sizeof(DenseParam<T, 5>);
+      return 2 * sizeof(T *) + sizeof(DenseIdx) + (sizeof(T) << 10);
+    default: return 2 * sizeof(T *) + sizeof(DenseIdx) + (sizeof(T) << 12);
+  }
+}
+
+size_t block_param_bytes(const Block &b, bool c128) {
+  return c128 ? param_bytes_t<double2>(b) : param_bytes_t<float2>(b);
+}
+
+cudaError_t launch_permute(void *amps, int n, bool c128, int qa, int qb, cudaStream_t s) {
+  Block b;
+  b.kind = BK_PERMUTE;
+  b.q[0] = qa < qb ? qa : qb;
+  b.q[1] = qa < qb ? qb : qa;
+  return launch_block(amps, n, c128, b, s, 256);
+}
+
+cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStream_t s) {
+  const size_t bytes = (size_t)(c128 ? 16 : 8) << n;
+  cudaError_t e = cudaMemsetAsync(amps, 0, bytes, s);
+  if (e != cudaSuccess) return e;
+  if (c128) k_set_one<double2><<<1, 1, 0, s>>>((double2 *)amps, idx);
+  else k_set_one<float2><<<1, 1, 0, s>>>((float2 *)amps, idx);
+  return cudaGetLastError();
+}
+
+int probs_grid(int n) {
+  const long long N = 1ll << n;
+  return grid_for(N, 256);
+}
+
+size_t probs_scratch_doubles(int n, int m) {
+  if (m > kProbsSmemBits) return 0;
+  return (size_t)probs_grid(n) << m;
+}
+
+cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int m, double *partial,
+                         double *out, cudaStream_t s) {
+  if (m < 0 || m > kMaxProbBits || m > n) return cudaErrorInvalidValue;
+  ProbsParam p;
+  p.n_amps = 1ll << n;
+  p.m = m;
+  for (int j = 0; j < m; j++) p.pos[j] = pos[j];
+  if (m <= kProbsSmemBits) {
+    const int grid = probs_grid(n);
+    const size_t smem = sizeof(double) << m;
+    if (c128) k_probs<double2><<<grid, 256, smem, s>>>((const double2 *)amps, p, partial);
+    else k_probs<float2><<<grid, 256, smem, s>>>((const float2 *)amps, p, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int nb = 1 << m;
+    k_probs_reduce<<<(nb + 255) / 256, 256, 0, s>>>(partial, grid, nb, out);
+    return cudaGetLastError();
+  }
+  const long long nb = 1ll << m;
+  const int grid = grid_for(nb, 256);
+  if (c128) k_probs_wide<double2><<<grid, 256, 0, s>>>((const double2 *)amps, p, n, out);
+  else k_probs_wide<float2><<<grid, 256, 0, s>>>((const float2 *)amps, p, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace qs

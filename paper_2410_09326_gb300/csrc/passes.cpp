@@ -1,0 +1,330 @@
+// Host passes: virtual swap, k-qubit fusion and block classification.
+//
+// Virtual swap (Sec. III-D): a SWAP gate exchanges two qubits' roles; instead
+// of moving 2^(n-1) amplitudes, the pass swaps the two entries of the
+// logical->physical map and later gates are renamed through it.
+//
+// Fusion generalises single-qubit gate merging (Sec. III-D, Z-Y
+// decomposition: consecutive one-qubit gates collapse into one unitary) and
+// QCOR's two-qubit block merging (Sec. IV, "all-on" set) to blocks of up to k
+// qubits whose product matrix is formed in FP64 on the host.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+namespace {
+
+constexpr double kEps = 1e-14;
+
+bool is_one(cd z) { return std::abs(z - cd(1, 0)) <= kEps; }
+bool is_zero(cd z) { return std::abs(z) <= kEps; }
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+// Position of physical qubit q inside the sorted list qs[0..w).
+int pos_of(const int *qs, int w, int q) {
+  for (int i = 0; i < w; i++)
+    if (qs[i] == q) return i;
+  return -1;
+}
+
+// Applies a gate's full matrix G (on local positions pos[0..m)) from the left
+// to every column of the block matrix M (2^w x 2^w, row-major).
+void left_multiply(std::vector<cd> &M, int w, const std::vector<cd> &G, const int *pos, int m) {
+  const int d = 1 << w, dg = 1 << m;
+  int gmask = 0;
+  for (int j = 0; j < m; j++) gmask |= 1 << pos[j];
+  std::vector<cd> v(dg), r(dg);
+  for (int col = 0; col < d; col++) {
+    for (int base = 0; base < d; base++) {
+      if (base & gmask) continue;
+      for (int l = 0; l < dg; l++) {
+        int idx = base;
+        for (int j = 0; j < m; j++)
+          if ((l >> j) & 1) idx |= 1 << pos[j];
+        v[l] = M[(size_t)idx * d + col];
+      }
+      for (int a = 0; a < dg; a++) {
+        cd acc = 0;
+        for (int b = 0; b < dg; b++) acc += G[(size_t)a * dg + b] * v[b];
+        r[a] = acc;
+      }
+      for (int l = 0; l < dg; l++) {
+        int idx = base;
+        for (int j = 0; j < m; j++)
+          if ((l >> j) & 1) idx |= 1 << pos[j];
+        M[(size_t)idx * d + col] = r[l];
+      }
+    }
+  }
+}
+
+struct Pending {
+  std::vector<int> members;  // indices into the physical gate list
+  uint64_t qmask = 0;
+  bool all_diag = true;
+};
+
+// Turns a group of gates into a classified Block (dense/diag/permute);
+// returns false when the product is the identity (nothing to launch).
+bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_permute, Block &out) {
+  int qs[64], w = 0;
+  for (int q = 0; q < 64; q++)
+    if ((p.qmask >> q) & 1) qs[w++] = q;
+  out = Block();
+  out.n_gates = (int)p.members.size();
+  const qs_gate &g0 = pg[p.members[0]];
+  if (out.n_gates == 1) {
+    out.first_op = g0.op;
+    out.meta = g0.op == QS_SWAP ? 3 : (op_info(g0.op).nq == 1 ? 0 : 1);
+  }
+  if (allow_permute && out.n_gates == 1 && g0.op == QS_SWAP) {
+    out.kind = BK_PERMUTE;
+    out.k = 2;
+    out.q[0] = std::min(g0.q[0], g0.q[1]);
+    out.q[1] = std::max(g0.q[0], g0.q[1]);
+    return true;
+  }
+  std::vector<cd> G;
+  if (p.all_diag) {
+    // diagonal table over the w qubits: product of every member's diagonal
+    std::vector<cd> tab((size_t)1 << w, cd(1, 0));
+    for (int gi : p.members) {
+      const qs_gate &g = pg[gi];
+      gate_full_matrix(g, G);
+      int m = g.nq, dg = 1 << m;
+      int pos[8];
+      for (int j = 0; j < m; j++) pos[j] = pos_of(qs, w, g.q[j]);
+      for (size_t l = 0; l < tab.size(); l++) {
+        int lg = 0;
+        for (int j = 0; j < m; j++) lg |= (int)((l >> pos[j]) & 1) << j;
+        tab[l] *= G[(size_t)lg * dg + lg];
+      }
+    }
+    // a qubit whose 0 half carries phase 1 everywhere acts as a control
+    uint64_t cmask = 0;
+    int keep[64], nk = 0;
+    for (int j = 0; j < w; j++) {
+      bool ctrl = true;
+      for (size_t l = 0; l < tab.size() && ctrl; l++)
+        if (!((l >> j) & 1) && !is_one(tab[l])) ctrl = false;
+      if (ctrl) cmask |= 1ull << qs[j];
+      else keep[nk++] = j;
+    }
+    int cbits = 0;
+    for (int j = 0; j < w; j++)
+      if ((cmask >> qs[j]) & 1) cbits |= 1 << j;
+    std::vector<cd> t2((size_t)1 << nk);
+    bool identity = true;
+    for (size_t l2 = 0; l2 < t2.size(); l2++) {
+      int l = cbits;
+      for (int j = 0; j < nk; j++)
+        if ((l2 >> j) & 1) l |= 1 << keep[j];
+      t2[l2] = tab[l];
+      if (!is_one(t2[l2])) identity = false;
+    }
+    if (identity) return false;
+    out.kind = BK_DIAG;
+    out.k = nk;
+    for (int j = 0; j < nk; j++) out.q[j] = qs[keep[j]];
+    out.cmask = cmask;
+    out.nctrl = popcount64(cmask);
+    out.mat = std::move(t2);
+    return true;
+  }
+  // dense product over the w qubits
+  const int d = 1 << w;
+  std::vector<cd> M((size_t)d * d, cd(0, 0));
+  for (int i = 0; i < d; i++) M[(size_t)i * d + i] = 1;
+  for (int gi : p.members) {
+    const qs_gate &g = pg[gi];
+    gate_full_matrix(g, G);
+    int pos[8];
+    for (int j = 0; j < g.nq; j++) pos[j] = pos_of(qs, w, g.q[j]);
+    left_multiply(M, w, G, pos, g.nq);
+  }
+  // control detection: block-diagonal in bit j with identity on the 0 half
+  uint64_t cmask = 0;
+  int keep[64], nk = 0;
+  for (int j = 0; j < w; j++) {
+    bool ctrl = true;
+    for (int r = 0; r < d && ctrl; r++)
+      for (int c = 0; c < d && ctrl; c++) {
+        cd z = M[(size_t)r * d + c];
+        int br = (r >> j) & 1, bc = (c >> j) & 1;
+        if (br != bc) { if (!is_zero(z)) ctrl = false; }
+        else if (br == 0) { if (r == c ? !is_one(z) : !is_zero(z)) ctrl = false; }
+      }
+    if (ctrl) cmask |= 1ull << qs[j];
+    else keep[nk++] = j;
+  }
+  int cbits = 0;
+  for (int j = 0; j < w; j++)
+    if ((cmask >> qs[j]) & 1) cbits |= 1 << j;
+  const int dk = 1 << nk;
+  std::vector<cd> R((size_t)dk * dk);
+  bool diag = true, identity = true;
+  auto expand = [&](int l2) {
+    int l = cbits;
+    for (int j = 0; j < nk; j++)
+      if ((l2 >> j) & 1) l |= 1 << keep[j];
+    return l;
+  };
+  for (int r = 0; r < dk; r++)
+    for (int c = 0; c < dk; c++) {
+      cd z = M[(size_t)expand(r) * d + expand(c)];
+      R[(size_t)r * dk + c] = z;
+      if (r != c && !is_zero(z)) diag = false, identity = false;
+      if (r == c && !is_one(z)) identity = false;
+    }
+  if (identity) return false;
+  out.cmask = cmask;
+  out.nctrl = popcount64(cmask);
+  out.k = nk;
+  for (int j = 0; j < nk; j++) out.q[j] = qs[keep[j]];
+  if (diag && nk <= QS_MAX_DIAG) {
+    out.kind = BK_DIAG;
+    out.mat.resize(dk);
+    for (int i = 0; i < dk; i++) out.mat[i] = R[(size_t)i * dk + i];
+  } else {
+    out.kind = BK_DENSE;
+    out.mat = std::move(R);
+  }
+  return true;
+}
+
+}  // namespace
+
+double block_bytes(const Block &b, int n, int amp_bytes) {
+  double amps = std::ldexp(1.0, n - b.nctrl);
+  if (b.kind == BK_PERMUTE) amps = std::ldexp(1.0, n - 1);
+  return 2.0 * amps * amp_bytes;
+}
+
+qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                     const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
+                     PlanStats &stats, std::string &err) {
+  plan.clear();
+  stats = PlanStats();
+  stats.gates_in = (int)n_gates;
+  // validation first: a bad gate leaves perm untouched
+  for (size_t i = 0; i < n_gates; i++) {
+    const qs_gate &g = gates[i];
+    if (g.op >= QS_N_GATE_TYPES) {
+      err = "gate " + std::to_string(i) + ": unknown op";
+      return QS_EINVAL;
+    }
+    if (g.nq != op_info(g.op).nq) {
+      err = "gate " + std::to_string(i) + ": qubit count does not match the op";
+      return QS_EINVAL;
+    }
+    for (int j = 0; j < g.nq; j++) {
+      if (g.q[j] >= n) {
+        err = "gate " + std::to_string(i) + ": qubit out of range";
+        return QS_EINVAL;
+      }
+      for (int k = 0; k < j; k++)
+        if (g.q[k] == g.q[j]) {
+          err = "gate " + std::to_string(i) + ": duplicate qubit";
+          return QS_EINVAL;
+        }
+    }
+    for (int j = 0; j < op_info(g.op).nparams; j++)
+      if (!std::isfinite(g.p[j])) {
+        err = "gate " + std::to_string(i) + ": non-finite angle";
+        return QS_EINVAL;
+      }
+  }
+  const bool vswap = flags & QS_VSWAP;
+  const bool fuse = flags & QS_FUSE;
+  const bool dfuse = flags & QS_DIAG;
+  int K = fuse ? QS_FUSE_K_OF(flags) : 0;
+  if (fuse && K == 0) K = 4;
+  if (K > QS_MAX_FUSE) {
+    err = "fusion width above QS_MAX_FUSE";
+    return QS_EUNSUPPORTED;
+  }
+  int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+
+  // (1) virtual swap and renaming to physical qubits
+  std::vector<qs_gate> pg;
+  pg.reserve(n_gates);
+  for (size_t i = 0; i < n_gates; i++) {
+    qs_gate g = gates[i];
+    if (vswap && g.op == QS_SWAP) {
+      std::swap(perm[g.q[0]], perm[g.q[1]]);
+      stats.swaps_absorbed++;
+      continue;
+    }
+    for (int j = 0; j < g.nq; j++) g.q[j] = (uint8_t)perm[g.q[j]];
+    pg.push_back(g);
+  }
+
+  // (2) grouping
+  std::vector<Pending> groups;
+  if (!fuse && !dfuse) {
+    groups.resize(pg.size());
+    for (size_t i = 0; i < pg.size(); i++) {
+      groups[i].members.push_back((int)i);
+      for (int j = 0; j < pg[i].nq; j++) groups[i].qmask |= 1ull << pg[i].q[j];
+      groups[i].all_diag = op_info(pg[i].op).diagonal;
+    }
+  } else {
+    // Greedy placement with commutation: a gate may join any group at or
+    // after the last group it cannot commute past. Two gates commute when
+    // both act diagonally on every qubit they share.
+    std::vector<int> last_any(64, -1), last_nd(64, -1);
+    for (size_t i = 0; i < pg.size(); i++) {
+      const qs_gate &g = pg[i];
+      const bool gdiag = op_info(g.op).diagonal;
+      uint64_t gmask = 0;
+      int lower = -1;
+      for (int j = 0; j < g.nq; j++) {
+        int q = g.q[j];
+        gmask |= 1ull << q;
+        lower = std::max(lower, gate_diag_on(g, j) ? last_nd[q] : last_any[q]);
+      }
+      int chosen = -1;
+      for (int b = std::max(lower, 0); b < (int)groups.size(); b++) {
+        const Pending &p = groups[b];
+        int width = popcount64(p.qmask | gmask);
+        bool nd = p.all_diag && gdiag;
+        int limit = nd ? (dfuse ? D : std::max(K, 1)) : K;
+        if (width <= limit) {
+          chosen = b;
+          break;
+        }
+      }
+      if (chosen < 0) {
+        groups.emplace_back();
+        chosen = (int)groups.size() - 1;
+      }
+      Pending &p = groups[chosen];
+      p.members.push_back((int)i);
+      p.qmask |= gmask;
+      p.all_diag = p.all_diag && gdiag;
+      for (int j = 0; j < g.nq; j++) {
+        int q = g.q[j];
+        last_any[q] = std::max(last_any[q], chosen);
+        if (!gate_diag_on(g, j)) last_nd[q] = std::max(last_nd[q], chosen);
+      }
+    }
+  }
+
+  // (3) products and classification
+  plan.reserve(groups.size());
+  for (const Pending &p : groups) {
+    if (p.members.empty()) continue;
+    Block b;
+    if (finish_block(pg, p, true, b)) plan.push_back(std::move(b));
+  }
+  for (Block &b : plan)
+    b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4;
+  return QS_OK;
+}
+
+}  // namespace qs

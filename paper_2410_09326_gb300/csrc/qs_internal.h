@@ -1,0 +1,103 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "qs.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// Gate table (OpenQASM 2 qelib1 definitions)
+// ---------------------------------------------------------------------------
+struct OpInfo {
+  const char *name;
+  int nq;        // controls + targets
+  int nparams;
+  int nctrl;     // leading control qubits
+  bool diagonal; // the whole gate is diagonal in the computational basis
+};
+
+const OpInfo &op_info(int op);
+int op_by_name(const char *name);  // -1 if unknown
+
+// Full matrix of a gate on its own qubits (controls embedded), local index
+// l = sum_j bit(q_j) << j over the gate's qubit order; (2^nq)^2 row-major.
+void gate_full_matrix(const qs_gate &g, std::vector<cd> &out);
+
+// True when the gate acts diagonally on its j-th qubit (a control qubit, or
+// any qubit of a diagonal gate): it then commutes with every other gate that
+// is diagonal on that qubit.
+bool gate_diag_on(const qs_gate &g, int j);
+
+// ---------------------------------------------------------------------------
+// Plan: the list of kernels one qs_apply_circuit call launches
+// ---------------------------------------------------------------------------
+enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2 };
+
+constexpr int kMaxFixed = 24;  // targets + controls handled by the index insert
+
+struct Block {
+  BlockKind kind = BK_DENSE;
+  int k = 0;                      // dense: targets; diag: table qubits; permute: 2
+  int q[QS_MAX_DIAG] = {0};       // physical qubits ascending (permute: a < b)
+  uint64_t cmask = 0;             // physical control bits (all must be 1)
+  int nctrl = 0;
+  std::vector<cd> mat;            // dense (2^k)^2 row-major; diag 2^k phases
+  int n_gates = 0;
+  int first_op = -1;              // op of a single-gate block
+  int meta = 4;                   // 0 one-qubit, 1 two-qubit, 3 swap, 4 fused
+  bool tc = false;
+};
+
+struct PlanStats {
+  int gates_in = 0;
+  int swaps_absorbed = 0;
+  int relocations = 0;
+};
+
+// Virtual swap + fusion + classification. Gates are logical; perm is the
+// state's logical->physical map, updated in place for absorbed SWAPs.
+// Returns QS_OK or QS_EINVAL (message in err).
+qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                     const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
+                     PlanStats &stats, std::string &err);
+
+double block_bytes(const Block &b, int n, int amp_bytes);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels.cu). All asynchronous on `s`.
+// ---------------------------------------------------------------------------
+struct DevInfo {
+  int sms = 0;
+  int max_threads_per_sm = 0;
+};
+const DevInfo &dev_info();
+
+cudaError_t launch_block(void *amps, int n, bool c128, const Block &b, cudaStream_t s, int threads);
+// Dense blocks too wide for the parameter space (k = 6, or k = 5 in c128)
+// read their matrix from device memory (row-major, the state's dtype).
+bool block_needs_dev_matrix(const Block &b, bool c128);
+// Bytes of gate data one block ships to the device: its kernel parameters
+// (matrix or phase table included) plus any matrix upload.
+size_t block_param_bytes(const Block &b, bool c128);
+cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
+                                     cudaStream_t s, int threads);
+cudaError_t launch_permute(void *amps, int n, bool c128, int a, int b, cudaStream_t s);
+cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStream_t s);
+
+// Marginal probabilities over m physical bits pos[0..m) (bin bit j = pos[j]).
+// partial: device scratch of probs_scratch_doubles(n, m) doubles; out: 2^m
+// doubles on the device.
+size_t probs_scratch_doubles(int n, int m);
+cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int m,
+                         double *partial, double *out, cudaStream_t s);
+
+}  // namespace qs

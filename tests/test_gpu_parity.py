@@ -1,0 +1,307 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (absolute L2 over all 2^n amplitudes, after placing the oracle's
+logical-order state through the reported permutation): 1e-5 for complex64
+(FP32 accumulation) and 1e-12 for complex128. The permutation must match the
+oracle's composed SWAP transpositions bit for bit whenever SWAPs are absorbed.
+At the benchmark's sizes (n = 28..30) the oracle cannot run whole, so those
+cases use closed forms (GHZ, QFT of a basis state) at sampled indices and
+properties that hold at any size (norm, circuit x inverse = |0...0>).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+import oracle
+import paper_2410_09326_gb300 as qs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {qs.QS_C64: 1e-5, qs.QS_C128: 1e-12}
+
+FLAGS = {
+    "plain": qs.QS_PLAIN,
+    "vswap": qs.QS_VSWAP,
+    "diag": qs.QS_DIAG,
+    "pgo_rules": qs.QS_PGO_RULES,
+    **{f"vswap_k{k}": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) for k in range(1, 7)},
+    **{f"vswap_k{k}_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)},
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return qs.load(build_if_missing=True)
+
+
+def gpu_run(n, gates, flags, dtype, init=None, logical=False):
+    st = qs.qs_alloc_state(n, dtype)
+    try:
+        if init is not None:
+            qs.qs_write_state(st, init.astype(np.complex64 if dtype == qs.QS_C64 else np.complex128))
+        qs.qs_apply_circuit(st, gates, flags)
+        perm = qs.qs_get_perm(st, n)
+        psi = qs.qs_read_state(st, n, dtype, logical_order=logical)
+        if logical:
+            assert list(qs.qs_get_perm(st, n)) == list(range(n))
+        return psi.astype(np.complex128), perm
+    finally:
+        qs.qs_free_state(st)
+
+
+def check(n, gates, flags, dtype, init=None):
+    text = cg.to_qasm(n, gates)
+    want, operm = oracle.simulate(text, init=init)
+    got, perm = gpu_run(n, qs.gates_to_array(gates), flags, dtype, init=init)
+    if flags & (qs.QS_VSWAP | qs.QS_PGO_RULES) and any(g[0] == "swap" for g in gates):
+        assert list(perm) == list(operm), (list(perm), list(operm))
+    elif not flags & (qs.QS_VSWAP | qs.QS_PGO_RULES):
+        assert list(perm) == list(range(n))
+    assert sorted(perm) == list(range(n))
+    err = np.linalg.norm(got - oracle.to_physical(want, perm))
+    assert err <= TOL[dtype], (err, flags)
+    return err
+
+
+@pytest.mark.parametrize("name", sorted(FLAGS))
+@pytest.mark.parametrize("index", [0, 1, 2])
+def test_config0_c128(name, index):
+    """n=12 complex128 layered random circuit with 10 SWAPs."""
+    n, gates = cg.config0_circuit(index)
+    check(n, gates, FLAGS[name], qs.QS_C128)
+
+
+@pytest.mark.parametrize("name", sorted(FLAGS))
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("n", [2, 5, 9, 14])
+def test_all_gate_types(name, dtype, n):
+    """Every gate type, targets low/high/mixed, controls above and below."""
+    rng = cg.SplitMix64(9000 + n)
+    gates = cg.all_gate_types_circuit(n, 120 if n > 9 else 200, rng)
+    init = None
+    if n == 9:
+        init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+        init /= np.linalg.norm(init)
+    check(n, gates, FLAGS[name], dtype, init=init)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_dense_block_every_target_class(dtype, k):
+    """One dense k-qubit block per target placement class at n=13."""
+    n = 13
+    rng = cg.SplitMix64(31 * k)
+    placements = [list(range(k)), list(range(n - k, n)), [0] + list(range(n - k + 1, n)),
+                  sorted(rng.shuffle(list(range(n)))[:k])]
+    for qubits in placements:
+        gates = []
+        for _ in range(3):
+            for q in qubits:
+                gates.append(("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]))
+            for a, b in zip(qubits[:-1], qubits[1:]):
+                gates.append(("cx", [a, b]))
+        # a control outside the block exercises the controlled subspace
+        check(n, gates, qs.QS_FUSE | qs.QS_FUSE_K(k), dtype)
+        outside = [q for q in range(n) if q not in qubits][0]
+        gates2 = [("h", [outside])] + [("ccx", [outside, qubits[0], qubits[-1]])] if k > 1 else gates
+        check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG, dtype)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_tiny_registers(n):
+    rng = cg.SplitMix64(77 + n)
+    gates = cg.all_gate_types_circuit(n, 50, rng)
+    for name in ("plain", "vswap_k6_diag", "vswap_k2"):
+        check(n, gates, FLAGS[name], qs.QS_C64)
+        check(n, gates, FLAGS[name], qs.QS_C128)
+
+
+def test_empty_circuit_and_identity():
+    for dtype in (qs.QS_C64, qs.QS_C128):
+        got, perm = gpu_run(6, qs.gates_to_array([]), qs.QS_PLAIN, dtype)
+        assert got[0] == 1 and np.count_nonzero(got) == 1
+        got, perm = gpu_run(6, qs.gates_to_array([("h", [2]), ("h", [2])]), FLAGS["vswap_k4_diag"], dtype)
+        assert got[0] == 1 and np.count_nonzero(got) == 1
+
+
+# ---------------------------------------------------------------------------
+# Closed forms at larger n
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["plain", "vswap", "vswap_k4_diag", "vswap_k6_diag"])
+def test_ghz_n24(name):
+    n = 24
+    got, perm = gpu_run(n, qs.gates_to_array(cg.ghz(n)), FLAGS[name], qs.QS_C64)
+    want = np.zeros(1 << n)
+    want[0] = want[-1] = 1 / math.sqrt(2)
+    assert np.linalg.norm(got - want) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["plain", "vswap", "vswap_k2_diag", "vswap_k5_diag"])
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_qft_closed_form_n18(name, dtype):
+    n = 18
+    gates, x = cg.qft(n, x=123457)
+    got, perm = gpu_run(n, qs.gates_to_array(gates), FLAGS[name], dtype, logical=True)
+    y = np.arange(1 << n)
+    want = np.exp(2j * np.pi * x * y / (1 << n)) / math.sqrt(1 << n)
+    assert np.linalg.norm(got - want) < TOL[dtype]
+
+
+def test_config1_random_n20_vs_oracle():
+    """The 30-layer random circuit with 5% SWAPs of the n=28 workload, at n=20."""
+    c = cg.config1_circuits(n=20)
+    n, gates = c["random"]
+    for name in ("plain", "vswap", "vswap_k3_diag", "vswap_k5_diag"):
+        check(n, gates, FLAGS[name], qs.QS_C64)
+
+
+# ---------------------------------------------------------------------------
+# Reductions
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_probs_and_norm(dtype):
+    n = 14
+    rng = cg.SplitMix64(5)
+    gates = cg.random_layered(n, 6, rng, n_swaps=5)
+    text = cg.to_qasm(n, gates)
+    want, _ = oracle.simulate(text)
+    st = qs.qs_alloc_state(n, dtype)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k4_diag"])
+        tol = 1e-6 if dtype == qs.QS_C64 else 1e-13
+        assert abs(qs.qs_norm(st) - 1.0) < tol
+        for qubits in ([0], [13], [3, 7], [12, 0, 5], list(range(10)), list(range(12)),
+                       list(range(13)), list(range(n)), [], [13, 12, 11, 10, 9, 8, 7, 6, 5, 4, 3, 2, 1, 0]):
+            got = qs.qs_measure_probs(st, qubits)
+            ref = oracle.probs(want, qubits) if qubits else np.array([1.0])
+            assert np.abs(got - ref).max() < tol, qubits
+    finally:
+        qs.qs_free_state(st)
+
+
+# ---------------------------------------------------------------------------
+# API behaviour
+# ---------------------------------------------------------------------------
+
+def test_errors_leave_state_usable():
+    st = qs.qs_alloc_state(5, qs.QS_C64)
+    try:
+        bad = qs.gates_to_array([("h", [0])])
+        bad[0]["q"][0] = 7
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_apply_circuit(st, bad, qs.QS_PLAIN)
+        assert e.value.status == qs.QS_EINVAL
+        with pytest.raises(qs.QsError):
+            qs.qs_measure_probs(st, [5])
+        with pytest.raises(qs.QsError):
+            qs.qs_measure_probs(st, [1, 1])
+        qs.qs_apply_circuit(st, qs.gates_to_array([("x", [4])]), qs.QS_PLAIN)
+        assert np.allclose(qs.qs_measure_probs(st, [4]), [0, 1])
+    finally:
+        qs.qs_free_state(st)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_alloc_state(35, qs.QS_C64)
+    assert e.value.status == qs.QS_EUNSUPPORTED
+
+
+def test_attach_torch_tensor_and_stream():
+    torch = pytest.importorskip("torch")
+    n = 12
+    buf = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    buf[0] = 1
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    st = qs.qs_attach_state(buf.data_ptr(), n, qs.QS_C64, stream=s)
+    try:
+        gates = cg.ghz(n)
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k3_diag"])
+        s.synchronize()
+        out = buf.cpu().numpy()
+        assert abs(out[0] - 1 / math.sqrt(2)) < 1e-6 and abs(out[-1] - 1 / math.sqrt(2)) < 1e-6
+    finally:
+        qs.qs_free_state(st)
+    assert buf.is_cuda  # memory stays the caller's
+
+
+def test_set_basis_and_profile_records():
+    n = 16
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        qs.qs_set_basis(st, 0b1011)
+        p = qs.qs_measure_probs(st, [0, 1, 2, 3])
+        assert p[0b1011] == 1.0
+        gates, x = cg.qft(n, x=99)
+        qs.qs_profile_reset(st)
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k2_diag"] | qs.QS_PROFILE)
+        summ, recs = qs.qs_profile(st)
+        assert summ.n_blocks == len(recs) > 0 and summ.swaps_absorbed == n // 2
+        assert all(r.ms > 0 for r in recs) and summ.total_ms > 0
+        assert summ.gates_seen == len(gates)
+        # counter table: H on every qubit once, CPhase on q_j j times as target
+        hcol = [summ.counters[q][0] for q in range(n)]
+        assert hcol == [1] * n
+        assert sum(summ.counters[q][11] for q in range(n)) == 2 * (n * (n - 1) // 2)
+        assert sum(r.n_gates for r in recs) <= len(gates)
+    finally:
+        qs.qs_free_state(st)
+
+
+# ---------------------------------------------------------------------------
+# Benchmark sizes: closed forms at sampled indices, properties at any size
+# ---------------------------------------------------------------------------
+
+def sampled_indices(n, count, seed):
+    rng = cg.SplitMix64(seed)
+    return np.array([rng.next() & ((1 << n) - 1) for _ in range(count)] + [0, (1 << n) - 1])
+
+
+@pytest.mark.parametrize("name", ["plain", "pgo"])
+def test_bench_size_n30_closed_forms(name):
+    import bench
+    n = 30
+    flags = bench.PLAIN_FLAGS if name == "plain" else bench.OPT_FLAGS
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        # GHZ: the whole probability mass on |0..0> and |1..1>
+        qs.qs_apply_circuit(st, qs.gates_to_array(cg.ghz(n)), flags)
+        p = qs.qs_measure_probs(st, [0, n - 1])
+        assert abs(p[0] - 0.5) < 1e-5 and abs(p[3] - 0.5) < 1e-5 and p[1] + p[2] < 1e-10
+        # QFT of a basis state: every amplitude has modulus 2^(-n/2); phases at
+        # sampled indices follow exp(2 pi i x y / 2^n)
+        qs.qs_set_basis(st, 0)
+        gates, x = cg.qft(n, rng=cg.SplitMix64(cg.seed_of(1, 0)))
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), flags)
+        perm = qs.qs_get_perm(st, n)
+        psi = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        ys = sampled_indices(n, 4096, 17)
+        phys = np.zeros_like(ys)
+        for l in range(n):
+            phys |= ((ys >> l) & 1) << int(perm[l])
+        want = np.exp(2j * np.pi * ((x * ys) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
+        assert np.abs(psi[phys] - want).max() < 1e-5 / math.sqrt(1 << n) * 64
+        assert abs(np.vdot(psi, psi).real - 1) < 1e-5
+    finally:
+        qs.qs_free_state(st)
+
+
+def test_bench_size_n30_random_times_inverse():
+    import bench
+    from tests.test_oracle_pins import _inverse
+    n = 30
+    c = cg.config1_circuits(n=n)
+    _, gates = c["random"]
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), bench.OPT_FLAGS)
+        assert abs(qs.qs_norm(st) - 1) < 1e-5
+        qs.qs_apply_circuit(st, qs.gates_to_array(_inverse(gates)), bench.OPT_FLAGS)
+        p = qs.qs_measure_probs(st, list(range(12)))
+        # back to |0...0>: amplitude error e gives 1 - p0 <= e^2 and p0 >= (1 - e)^2
+        assert p[0] > (1 - 1e-5) ** 2
+    finally:
+        qs.qs_free_state(st)

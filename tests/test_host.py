@@ -1,0 +1,233 @@
+"""Host-side checks of the library (no GPU): exported symbols, the IR parser,
+and the virtual-swap / fusion passes.
+
+The passes are checked by applying the planned blocks' FP64 matrices to a
+state in numpy (a contraction written here, independent of both the CUDA
+kernels and the oracle's loops) and comparing with the oracle. Every fusion
+is a valid answer as long as the product matches; no partition is assumed.
+"""
+
+import ctypes
+import math
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import circuitgen as cg
+import oracle
+import paper_2410_09326_gb300 as qs
+from paper_2410_09326_gb300 import build as qbuild
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return qs.load(build_if_missing=True)
+
+
+def header_functions():
+    text = open(qbuild.INC + "/qs.h").read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z_0-9]+)\s*\(", text)) - {"QS_FUSE_K"})
+
+
+def test_every_declared_symbol_is_exported():
+    names = header_functions()
+    assert "qs_apply_circuit" in names and "qs_measure_probs" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", qs.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(qs.load(), n)
+
+
+def test_library_built_for_sm_103a():
+    out = subprocess.run(["cuobjdump", "--list-elf", qs.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+
+
+def test_parser_matches_generator():
+    rng = cg.SplitMix64(3)
+    gates = cg.all_gate_types_circuit(7, 300, rng)
+    n, arr = qs.qs_parse_qasm(cg.to_qasm(7, gates))
+    assert n == 7 and arr.size == len(gates)
+    for g, a in zip(gates, arr):
+        assert qs.OPS[a["op"]] == g[0]
+        assert list(a["q"][: a["nq"]]) == list(g[1])
+        ps = g[2] if len(g) > 2 else []
+        assert list(a["p"][: len(ps)]) == list(ps)  # exact round trip of 17 digits
+
+
+@pytest.mark.parametrize("bad", ["qreg q[2];\nh q[2];\n", "qreg q[2];\ncx q[0],q[0];\n",
+                                 "qreg q[2];\nrz q[0];\n", "qreg q[2];\nfoo q[0];\n", "h q[0];\n",
+                                 "qreg q[2];\nh q[0]\n", "qreg q[41];\n"])
+def test_parser_rejects(bad):
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_parse_qasm(bad)
+    assert e.value.status == qs.QS_EINVAL
+
+
+def test_ids_follow_the_paper():
+    # Sec. III-C: H is type 0 and CPhase type 11 in the context records
+    assert qs.OPS.index("h") == 0 and qs.OPS.index("cp") == 11
+    assert qs.OPS[:3] == ["h", "s", "t"] and len(qs.OPS) == 33
+
+
+# ---------------------------------------------------------------------------
+# Passes
+# ---------------------------------------------------------------------------
+
+def apply_block(psi, n, rec, mat):
+    """Applies one planned block to a physical-order state (numpy, FP64)."""
+    idx = np.arange(1 << n, dtype=np.int64)
+    if rec.kind == 2:  # exchange of physical bits a, b
+        a, b = rec.qubits[0], rec.qubits[1]
+        flip = ((idx >> a) & 1) ^ ((idx >> b) & 1)
+        return psi[idx ^ (flip << a) ^ (flip << b)]
+    qubits = [int(rec.qubits[j]) for j in range(rec.k)]
+    cm = int(rec.cmask)
+    on = (idx & cm) == cm
+    out = psi.copy()
+    if rec.kind == 1:
+        local = np.zeros(1 << n, dtype=np.int64)
+        for j, q in enumerate(qubits):
+            local |= ((idx >> q) & 1) << j
+        out[on] = psi[on] * mat[local[on]]
+        return out
+    d = 1 << rec.k
+    tmask = sum(1 << q for q in qubits)
+    bases = idx[((idx & tmask) == 0) & on]
+    offs = np.array([sum(((l >> j) & 1) << q for j, q in enumerate(qubits)) for l in range(d)],
+                    dtype=np.int64)
+    sel = bases[:, None] + offs[None, :]
+    out[sel] = psi[sel] @ mat.T
+    return out
+
+
+def plan_state(n, gates, flags, init=None):
+    recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), flags)
+    psi = np.zeros(1 << n, dtype=complex)
+    psi[0] = 1
+    if init is not None:
+        psi = init.copy()
+    for r, m in zip(recs, mats):
+        psi = apply_block(psi, n, r, m)
+    return psi, perm, recs
+
+
+ALL_FLAGS = [qs.QS_PLAIN, qs.QS_VSWAP, qs.QS_DIAG, qs.QS_VSWAP | qs.QS_DIAG] + [
+    qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | d for k in range(1, 7) for d in (0, qs.QS_DIAG)] + [
+    qs.QS_FUSE | qs.QS_FUSE_K(4), qs.QS_PGO_RULES]
+
+
+@pytest.mark.parametrize("flags", ALL_FLAGS)
+def test_plan_reproduces_oracle_all_gate_types(flags):
+    n = 7
+    rng = cg.SplitMix64(4242)
+    gates = cg.all_gate_types_circuit(n, 250, rng)
+    want, operm = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, recs = plan_state(n, gates, flags)
+    if flags & qs.QS_VSWAP or flags & qs.QS_PGO_RULES:
+        assert list(perm) == list(operm)
+    else:
+        assert list(perm) == list(range(n))
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+
+
+@pytest.mark.parametrize("flags", ALL_FLAGS[::3])
+def test_plan_reproduces_oracle_qft_and_config0(flags):
+    n = 8
+    gates, x = cg.qft(n, x=77)
+    want, operm = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, _ = plan_state(n, gates, flags)
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+    n, gates = cg.config0_circuit(1)
+    want, operm = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, _ = plan_state(n, gates, flags)
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+
+
+def test_fusion_reduces_blocks():
+    n, gates = cg.config0_circuit(0)
+    arr = qs.gates_to_array(gates)
+    counts = {k: len(qs.qs_plan(n, arr, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k))[0]) for k in range(1, 7)}
+    plain = len(qs.qs_plan(n, arr, qs.QS_PLAIN)[0])
+    assert plain == len(gates)
+    assert counts[1] < plain and all(counts[k + 1] <= counts[k] for k in range(1, 6))
+
+
+def test_diagonal_runs_fuse_wide():
+    # QFT: the CPhase ladder after each H is one diagonal run
+    n = 12
+    gates, _ = cg.qft(n, x=5, swaps=False)
+    recs, mats, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(1) | qs.QS_DIAG)
+    diag = [r for r in recs if r.kind == 1]
+    assert diag and max(r.k + r.nctrl for r in diag) >= 8
+
+
+def test_controls_are_detected():
+    recs, mats, _ = qs.qs_plan(5, qs.gates_to_array([("ccx", [0, 3, 1]), ("cp", [2, 4], [0.3])]), qs.QS_PLAIN)
+    assert recs[0].kind == 0 and recs[0].k == 1 and recs[0].cmask == 0b1001 and recs[0].qubits[0] == 1
+    # CPhase acts only where both bits are 1: a one-entry table with two controls
+    assert recs[1].kind == 1 and recs[1].k == 0 and recs[1].cmask == 0b10100
+    assert np.isclose(mats[1][0], np.exp(0.3j))
+
+
+def test_identity_products_are_dropped():
+    recs, _, _ = qs.qs_plan(3, qs.gates_to_array([("cx", [0, 1]), ("cx", [0, 1]), ("h", [2]), ("h", [2])]),
+                            qs.QS_FUSE | qs.QS_FUSE_K(2))
+    assert recs == []
+
+
+def test_plan_rejects_bad_gates():
+    arr = qs.gates_to_array([("h", [0])])
+    arr[0]["q"][0] = 9
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_plan(4, arr, qs.QS_PLAIN)
+    assert e.value.status == qs.QS_EINVAL
+    arr = qs.gates_to_array([("cx", [0, 1])])
+    arr[0]["nq"] = 1
+    with pytest.raises(qs.QsError):
+        qs.qs_plan(4, arr, qs.QS_PLAIN)
+    with pytest.raises(qs.QsError) as e:
+        qs.qs_plan(4, qs.gates_to_array([("h", [0])]), qs.QS_FUSE | qs.QS_FUSE_K(7))
+    assert e.value.status == qs.QS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("flags", [qs.QS_PLAIN, qs.QS_VSWAP, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(3),
+                                   qs.QS_FUSE | qs.QS_FUSE_K(2) | qs.QS_DIAG])
+def test_plan_perm_and_counts(flags):
+    n, gates = cg.config0_circuit(0)
+    arr = qs.gates_to_array(gates)
+    recs, mats, perm = qs.qs_plan(n, arr, flags)
+    _, operm = oracle.simulate(cg.to_qasm(n, gates))
+    if flags & qs.QS_VSWAP:
+        assert list(perm) == list(operm)
+    else:
+        assert list(perm) == list(range(n))
+    assert sum(r.n_gates for r in recs) <= len(gates)
+    k_max = (flags >> 16) & 15 if flags & qs.QS_FUSE else 3
+    for r, m in zip(recs, mats):
+        if r.kind == 0:
+            assert r.k <= max(k_max, 3)
+            assert np.allclose(m.conj().T @ m, np.eye(1 << r.k), atol=1e-12)
+        elif r.kind == 1:
+            assert r.k <= qs.QS_MAX_DIAG and np.allclose(np.abs(m), 1, atol=1e-12)
+
+
+def test_swaps_absorbed_count():
+    n = 6
+    gates = [("h", [0]), ("swap", [0, 5]), ("cx", [5, 1]), ("swap", [1, 2])]
+    recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP)
+    assert len(recs) == 2 and all(r.kind != 2 for r in recs)
+    assert list(perm) == [5, 2, 1, 3, 4, 0]
+    # the CX on logical (5 -> 1) runs on physical (0 -> 1)... after the
+    # first swap logical 5 lives at physical 0
+    assert recs[1].qubits[0] == 1 and recs[1].nctrl == 1
+    recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_PLAIN)
+    assert [r.kind for r in recs] == [0, 2, 0, 2]
