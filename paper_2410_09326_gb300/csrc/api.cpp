@@ -38,6 +38,7 @@ struct qs_state {
   void *h_mats = nullptr;  // pinned staging for d_mats
   size_t h_mats_cap = 0;
   cudaEvent_t mats_copied = nullptr;
+  int *d_err = nullptr;  // set by kernels whose bounded waits expired
   // profiling (Sec. III-C): counters per logical qubit and gate type, the
   // longest run of consecutive one-qubit gates per qubit, per-block records
   int64_t counters[QS_MAX_QUBITS][QS_N_GATE_TYPES] = {{0}};
@@ -65,6 +66,21 @@ qs_status fail(qs_status s, const std::string &msg) {
 qs_status cuda_fail(qs_state *st, cudaError_t e, const char *where) {
   if (st) st->bad = true;
   return fail(QS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// After a stream synchronisation: a kernel that gave up a bounded wait left
+// 1 in the error word; report it once and clear it.
+qs_status check_device_error(qs_state *st) {
+  if (!st->d_err) return QS_OK;
+  int h = 0;
+  cudaError_t e = cudaMemcpy(&h, st->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return QS_ECUDA;
+  if (h) {
+    cudaMemset(st->d_err, 0, sizeof(int));
+    last_error_ref() = "a device-side wait timed out; results of the last apply are not valid";
+    return QS_ETIMEOUT;
+  }
+  return QS_OK;
 }
 
 qs_status check_state(const qs_state *st) {
@@ -155,7 +171,7 @@ uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts
   // merging: a run of consecutive one-qubit gates above the threshold, or
   // (GPU reading) any circuit with more than one gate, since each fused gate
   // saves a full pass over the state
-  if (max_run > o.merge_run || n_gates > 1) f |= QS_FUSE | QS_FUSE_K(4) | QS_DIAG;
+  if (max_run > o.merge_run || n_gates > 1) f |= QS_FUSE | QS_FUSE_K(5) | QS_DIAG | QS_TC;
   (void)t_count;
   (void)dense;
   return f;
@@ -217,6 +233,7 @@ void qs_free_state(qs_state *st) {
   if (st->d_mats) cudaFree(st->d_mats);
   if (st->h_mats) cudaFreeHost(st->h_mats);
   if (st->mats_copied) cudaEventDestroy(st->mats_copied);
+  if (st->d_err) cudaFree(st->d_err);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
   delete st;
 }
@@ -272,8 +289,10 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   for (size_t i = 0; i < plan.size(); i++)
     if (block_needs_dev_matrix(plan[i], c128)) {
       mat_off[i] = mat_bytes;
-      mat_bytes += plan[i].mat.size() * (size_t)ab;
+      mat_bytes += (block_dev_matrix_bytes(plan[i], c128) + 255) & ~(size_t)255;
     }
+  bool any_tc = false;
+  for (const Block &b : plan) any_tc |= b.tc && !c128;
   cudaError_t e;
   if (mat_bytes) {
     if (st->mats_copied) {
@@ -302,25 +321,19 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
       st->d_mats = dm;
       st->mats_cap = mat_bytes;
     }
-    for (size_t i = 0; i < plan.size(); i++) {
-      if (mat_off[i] == (size_t)-1) continue;
-      unsigned char *h = (unsigned char *)st->h_mats + mat_off[i];
-      for (size_t k = 0; k < plan[i].mat.size(); k++) {
-        if (c128) {
-          double v[2] = {plan[i].mat[k].real(), plan[i].mat[k].imag()};
-          std::memcpy(h + k * 16, v, 16);
-        } else {
-          float v[2] = {(float)plan[i].mat[k].real(), (float)plan[i].mat[k].imag()};
-          std::memcpy(h + k * 8, v, 8);
-        }
-      }
-    }
+    for (size_t i = 0; i < plan.size(); i++)
+      if (mat_off[i] != (size_t)-1) fill_dev_matrix(plan[i], c128, (unsigned char *)st->h_mats + mat_off[i]);
     e = cudaMemcpyAsync(st->d_mats, st->h_mats, mat_bytes, cudaMemcpyHostToDevice, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
     e = cudaEventRecord(st->mats_copied, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
   }
 
+  if (any_tc && !st->d_err) {
+    e = cudaMalloc((void **)&st->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(st->d_err, 0, sizeof(int), st->stream);
+    if (e != cudaSuccess) return fail(QS_ENOMEM, "error word allocation failed");
+  }
   const bool prof = flags & QS_PROFILE;
   if (prof) {
     while (st->events.size() < plan.size() + 1) {
@@ -338,7 +351,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   for (size_t i = 0; i < plan.size(); i++) {
     const Block &b = plan[i];
     const void *dm = mat_off[i] == (size_t)-1 ? nullptr : (const unsigned char *)st->d_mats + mat_off[i];
-    e = launch_block_with_matrix(st->amps, st->n, c128, b, dm, st->stream, o.threads);
+    e = launch_block_with_matrix(st->amps, st->n, c128, b, dm, st->d_err, st->stream, o.threads);
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit launch");
     if (prof) {
       e = cudaEventRecord(st->events[i + 1], st->stream);
@@ -497,7 +510,7 @@ qs_status qs_measure_probs(qs_state *st, const int *logical_qubits, int m, doubl
   if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, st->d_out, nb * sizeof(double), cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e, "qs_measure_probs");
-  return QS_OK;
+  return check_device_error(st);
 }
 
 qs_status qs_norm(qs_state *st, double *host_out) { return qs_measure_probs(st, nullptr, 0, host_out); }
@@ -524,7 +537,7 @@ qs_status qs_read_state(qs_state *st, void *host_out, int logical_order) {
   e = cudaMemcpyAsync(host_out, st->amps, (size_t)amp_bytes(st) << st->n, cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
-  return QS_OK;
+  return check_device_error(st);
 }
 
 qs_status qs_write_state(qs_state *st, const void *host_in) {

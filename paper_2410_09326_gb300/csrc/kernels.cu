@@ -66,6 +66,63 @@ __global__ void __launch_bounds__(256) k_diag(T *__restrict__ a, const __grid_co
   }
 }
 
+// Chunked diagonal pass, used when no control bit lies below bit kChunkBits:
+// the compacted index space splits into chunks of 2^kChunkBits amplitudes
+// that are contiguous in memory. The table index of an amplitude is
+// (index bits of the chunk base on table qubits >= kChunkBits) OR
+// lo_tab[offset within the chunk], so the per-amplitude work is one shared
+// load, one table load and a complex multiply; each thread moves 16 bytes
+// per access.
+constexpr int kChunkBits = 10;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_chunk(T *__restrict__ a, const __grid_constant__ DiagParam<T> p) {
+  using R = typename Real<T>::type;
+  constexpr int CH = 1 << kChunkBits;
+  constexpr int PER = sizeof(T) == 8 ? 2 : 1;  // amplitudes per 16-byte access
+  constexpr int LANES = CH / PER;              // accesses per chunk
+  __shared__ T tab[1 << QS_MAX_DIAG];
+  __shared__ uint16_t lo_tab[CH];
+  const int tn = 1 << p.k;
+  for (int i = threadIdx.x; i < tn; i += blockDim.x) tab[i] = p.tab[i];
+  for (int o = threadIdx.x; o < CH; o += blockDim.x) {
+    int l = 0;
+    for (int b = 0; b < p.k; b++)
+      if (p.tq[b] < kChunkBits) l |= ((o >> p.tq[b]) & 1) << b;
+    lo_tab[o] = (uint16_t)l;
+  }
+  __syncthreads();
+  const long long n_chunks = p.n_amps >> kChunkBits;
+  const long long total = n_chunks * LANES;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const long long chunk = t / LANES;
+    const int o = (int)(t - chunk * LANES) * PER;
+    const uint64_t cbase = insert_zeros((uint64_t)chunk << kChunkBits, p.fixed, p.nf) | p.cmask;
+    int lhi = 0;
+    for (int b = 0; b < p.k; b++)
+      if (p.tq[b] >= kChunkBits) lhi |= (int)((cbase >> p.tq[b]) & 1) << b;
+    T *ptr = a + cbase + o;
+    if constexpr (PER == 2) {
+      float4 v = *reinterpret_cast<const float4 *>(ptr);
+      const T w0 = tab[lhi | lo_tab[o]], w1 = tab[lhi | lo_tab[o + 1]];
+      float4 y;
+      y.x = fmaf(w0.x, v.x, -w0.y * v.y);
+      y.y = fmaf(w0.x, v.y, w0.y * v.x);
+      y.z = fmaf(w1.x, v.z, -w1.y * v.w);
+      y.w = fmaf(w1.x, v.w, w1.y * v.z);
+      *reinterpret_cast<float4 *>(ptr) = y;
+    } else {
+      const T v = *ptr;
+      const T w = tab[lhi | lo_tab[o]];
+      T y;
+      y.x = fma((R)w.x, v.x, -(R)w.y * v.y);
+      y.y = fma((R)w.x, v.y, (R)w.y * v.x);
+      *ptr = y;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_permute(T *__restrict__ a, long long n_pairs, int qa, int qb) {
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -185,7 +242,13 @@ cudaError_t run_block(T *a, int n, const Block &b, const void *dev_mat, cudaStre
     fill_fixed(b, p.fixed, p.nf);
     p.k = b.k;
     for (int j = 0; j < b.k; j++) p.tq[j] = b.q[j];
-    k_diag<T><<<grid_for(p.n_amps, threads), threads, 0, s>>>(a, p);
+    const bool chunked = (b.cmask & ((1ull << kChunkBits) - 1)) == 0 && n - b.nctrl >= kChunkBits;
+    if (chunked) {
+      const long long accesses = p.n_amps / (sizeof(T) == 8 ? 2 : 1);
+      k_diag_chunk<T><<<grid_for(accesses, threads), threads, 0, s>>>(a, p);
+    } else {
+      k_diag<T><<<grid_for(p.n_amps, threads), threads, 0, s>>>(a, p);
+    }
     return cudaGetLastError();
   }
   if constexpr (sizeof(T) == 8) return run_dense_c64((float2 *)a, n, b, dev_mat, s, threads);
@@ -212,18 +275,43 @@ const DevInfo &dev_info() {
 }
 
 bool block_needs_dev_matrix(const Block &b, bool c128) {
-  return b.kind == BK_DENSE && (b.k == 6 || (c128 && b.k == 5));
+  if (b.kind != BK_DENSE) return false;
+  if (b.tc && !c128) return true;
+  return b.k == 6 || (c128 && b.k == 5);
+}
+
+size_t block_dev_matrix_bytes(const Block &b, bool c128) {
+  if (!block_needs_dev_matrix(b, c128)) return 0;
+  if (b.tc && !c128) return tc_b_floats(b.k) * sizeof(float);
+  return b.mat.size() * (c128 ? 16 : 8);
+}
+
+void fill_dev_matrix(const Block &b, bool c128, void *host_out) {
+  if (b.tc && !c128) {
+    tc_build_b(b, (float *)host_out);
+    return;
+  }
+  for (size_t k = 0; k < b.mat.size(); k++) {
+    if (c128) {
+      double v[2] = {b.mat[k].real(), b.mat[k].imag()};
+      std::memcpy((char *)host_out + k * 16, v, 16);
+    } else {
+      float v[2] = {(float)b.mat[k].real(), (float)b.mat[k].imag()};
+      std::memcpy((char *)host_out + k * 8, v, 8);
+    }
+  }
 }
 
 cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
-                                     cudaStream_t s, int threads) {
+                                     int *err, cudaStream_t s, int threads) {
   if (threads <= 0) threads = 256;
+  if (b.kind == BK_DENSE && b.tc && !c128) return run_dense_tc((float2 *)amps, n, b, dev_mat, err, s);
   if (c128) return run_block<double2>((double2 *)amps, n, b, dev_mat, s, threads);
   return run_block<float2>((float2 *)amps, n, b, dev_mat, s, threads);
 }
 
 cudaError_t launch_block(void *amps, int n, bool c128, const Block &b, cudaStream_t s, int threads) {
-  return launch_block_with_matrix(amps, n, c128, b, nullptr, s, threads);
+  return launch_block_with_matrix(amps, n, c128, b, nullptr, nullptr, s, threads);
 }
 
 template <typename T> size_t param_bytes_t(const Block &b) {

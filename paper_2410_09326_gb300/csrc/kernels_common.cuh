@@ -164,6 +164,13 @@ cudaError_t run_dense_smem(T *a, int n, const Block &b, const T *dev_mat, cudaSt
   return cudaGetLastError();
 }
 
+// Tensor-core path (tc_dense.cu): dense blocks with 4 or 5 targets, c64.
+// dev_b holds tc_b_floats(k) floats written by tc_build_b; err is a device
+// error word set to 1 when a bounded wait expires.
+size_t tc_b_floats(int k);
+void tc_build_b(const Block &b, float *out);
+cudaError_t run_dense_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s);
+
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 cudaError_t run_dense_c128(double2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 

@@ -323,7 +323,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     if (finish_block(pg, p, true, b)) plan.push_back(std::move(b));
   }
   for (Block &b : plan)
-    b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4;
+    b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= 5;
   return QS_OK;
 }
 

@@ -84,12 +84,16 @@ const DevInfo &dev_info();
 cudaError_t launch_block(void *amps, int n, bool c128, const Block &b, cudaStream_t s, int threads);
 // Dense blocks too wide for the parameter space (k = 6, or k = 5 in c128)
 // read their matrix from device memory (row-major, the state's dtype).
+// Tensor-core blocks read their split real embedding from device memory too.
 bool block_needs_dev_matrix(const Block &b, bool c128);
+size_t block_dev_matrix_bytes(const Block &b, bool c128);
+void fill_dev_matrix(const Block &b, bool c128, void *host_out);
 // Bytes of gate data one block ships to the device: its kernel parameters
 // (matrix or phase table included) plus any matrix upload.
 size_t block_param_bytes(const Block &b, bool c128);
+// err: device error word for kernels with bounded waits (tensor-core path).
 cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
-                                     cudaStream_t s, int threads);
+                                     int *err, cudaStream_t s, int threads);
 cudaError_t launch_permute(void *amps, int n, bool c128, int a, int b, cudaStream_t s);
 cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStream_t s);
 

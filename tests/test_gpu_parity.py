@@ -29,6 +29,8 @@ FLAGS = {
     "pgo_rules": qs.QS_PGO_RULES,
     **{f"vswap_k{k}": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) for k in range(1, 7)},
     **{f"vswap_k{k}_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)},
+    **{f"vswap_k{k}_tc": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC for k in (4, 5, 6)},
+    **{f"vswap_k{k}_tc_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC | qs.QS_DIAG for k in (4, 5)},
 }
 
 
@@ -88,9 +90,10 @@ def test_all_gate_types(name, dtype, n):
     check(n, gates, FLAGS[name], dtype, init=init)
 
 
+@pytest.mark.parametrize("tc", [0, qs.QS_TC])
 @pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
-def test_dense_block_every_target_class(dtype, k):
+def test_dense_block_every_target_class(dtype, k, tc):
     """One dense k-qubit block per target placement class at n=13."""
     n = 13
     rng = cg.SplitMix64(31 * k)
@@ -104,10 +107,10 @@ def test_dense_block_every_target_class(dtype, k):
             for a, b in zip(qubits[:-1], qubits[1:]):
                 gates.append(("cx", [a, b]))
         # a control outside the block exercises the controlled subspace
-        check(n, gates, qs.QS_FUSE | qs.QS_FUSE_K(k), dtype)
+        check(n, gates, qs.QS_FUSE | qs.QS_FUSE_K(k) | tc, dtype)
         outside = [q for q in range(n) if q not in qubits][0]
         gates2 = [("h", [outside])] + [("ccx", [outside, qubits[0], qubits[-1]])] if k > 1 else gates
-        check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG, dtype)
+        check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | tc, dtype)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3])
@@ -146,8 +149,9 @@ def test_qft_closed_form_n18(name, dtype):
     n = 18
     gates, x = cg.qft(n, x=123457)
     got, perm = gpu_run(n, qs.gates_to_array(gates), FLAGS[name], dtype, logical=True)
-    y = np.arange(1 << n)
-    want = np.exp(2j * np.pi * x * y / (1 << n)) / math.sqrt(1 << n)
+    y = np.arange(1 << n, dtype=np.int64)
+    # reduce x*y mod 2^n first: the FP64 phase argument stays exact
+    want = np.exp(2j * np.pi * ((x * y) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
     assert np.linalg.norm(got - want) < TOL[dtype]
 
 
@@ -155,8 +159,21 @@ def test_config1_random_n20_vs_oracle():
     """The 30-layer random circuit with 5% SWAPs of the n=28 workload, at n=20."""
     c = cg.config1_circuits(n=20)
     n, gates = c["random"]
-    for name in ("plain", "vswap", "vswap_k3_diag", "vswap_k5_diag"):
+    for name in ("plain", "vswap", "vswap_k3_diag", "vswap_k5_diag", "vswap_k4_tc_diag", "vswap_k5_tc_diag"):
         check(n, gates, FLAGS[name], qs.QS_C64)
+
+
+def test_tc_blocks_really_run_on_tensor_cores():
+    n = 16
+    rng = cg.SplitMix64(12)
+    gates = cg.random_layered(n, 8, rng, one_q=("u3",), two_q=("cx", "cz"))
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k5_tc_diag"] | qs.QS_PROFILE)
+        summ, recs = qs.qs_profile(st)
+        assert any(r.tc for r in recs) and all(r.tc == (r.kind == 0 and r.k in (4, 5)) for r in recs)
+    finally:
+        qs.qs_free_state(st)
 
 
 # ---------------------------------------------------------------------------
