@@ -251,7 +251,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 (f32 fused products, f64 reductions)", "data": "synthetic (seeded circuits)",
         "config": {"workload": "n=30 c64: GHZ + QFT(basis state, swap network) + 30-layer random (5% SWAP), "
-                               "PGO rules -> vswap + k<=4 fusion + diagonal runs; FP64 probs of 16 qubits",
+                               "PGO rules -> vswap + k<=5 fusion (tensor cores for k=4,5) + diagonal runs; "
+                               "FP64 probs of 16 qubits",
                    "n_qubits": n, "circuits": [c[0] for c in circuits],
                    "gates": [qs.qs_parse_qasm(t)[1].size for _, t in circuits],
                    "l2": "state 8 GiB >> 129 MB L2 (no flush needed)", "parallelism": f"replicas x{world}"},
@@ -276,8 +277,9 @@ def run_ours(args):
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of that kernel,
-# scaled to n=30; None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {}
+# scaled to n=30 by the amplitudes processed (profiles/k_dense_tc5_n26.md:
+# 1012.1 MB at n=26 -> x16); None where no capture of the current kernel exists.
+TRAFFIC_PER_LAUNCH = {"k_dense_k5_tc": 16.19e9}
 
 
 # ---------------------------------------------------------------------------
@@ -356,6 +358,48 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+CASES = ("tc5", "tc4", "dense3", "diag10", "permute", "probs")
+
+
+def run_case(args):
+    """A few launches of one kernel kind on a small state (profiling aid):
+    prints one line with the kernel's event-timed GB/s."""
+    import torch
+    import paper_2410_09326_gb300 as qs
+    qs.load(build_if_missing=True)
+    n = args.n
+    rng = cg.SplitMix64(77)
+    k = {"tc5": 5, "tc4": 4, "dense3": 3}.get(args.case, 0)
+    if k:
+        qubits = [1, 6, 11, 16, 21][:k] if n > 21 else list(range(0, 2 * k, 2))
+        gates = [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+        gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        flags = qs.QS_FUSE | qs.QS_FUSE_K(k) | (qs.QS_TC if args.case.startswith("tc") else 0)
+    elif args.case == "diag10":
+        qs_ = list(range(n - 10, n))
+        gates = [("cp", [a, b], [rng.uniform(0, 3)]) for a, b in zip(qs_[:-1], qs_[1:])] + [("rz", [q], [0.3]) for q in qs_]
+        flags = qs.QS_DIAG
+    elif args.case == "permute":
+        gates = [("swap", [3, n - 2])]
+        flags = qs.QS_PLAIN
+    else:
+        gates = []
+        flags = qs.QS_PLAIN
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    arr = qs.gates_to_array(gates)
+    for _ in range(args.launches):
+        if args.case == "probs":
+            qs.qs_measure_probs(st, list(range(10)))
+        else:
+            qs.qs_apply_circuit(st, arr, flags | qs.QS_PROFILE)
+    if args.case != "probs":
+        summ, recs = qs.qs_profile(st)
+        print(json.dumps({"case": args.case, "n": n, "blocks": [(kernel_name(r), round(r.ms, 4),
+                          round(r.bytes / r.ms / 1e6, 1)) for r in recs]}))
+    qs.qs_free_state(st)
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +408,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-gates", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=CASES, help="profiling aid: launch one kernel kind only")
+    ap.add_argument("--n", type=int, default=26)
+    ap.add_argument("--launches", type=int, default=3)
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
