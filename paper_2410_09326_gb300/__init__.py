@@ -114,6 +114,8 @@ def load(build_if_missing=False):
         "qs_write_state": (ctypes.c_int, [vp, vp]),
         "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "qs_last_error": (ctypes.c_char_p, []),
+        "qs_probs_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.c_int, vp, vp]),
         "qs_plan": (ctypes.c_int, [ctypes.c_int, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts),
                                    ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(qs_block_record), sz,
                                    ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_double), sz,
@@ -218,6 +220,15 @@ def qs_measure_probs(st, logical_qubits):
     _check(load().qs_measure_probs(st, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(q),
                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def qs_probs_noalloc(dev_amps, n, dtype, phys_bits, dev_out, stream=None):
+    """No-allocation marginal probabilities on raw device pointers (asynchronous;
+    dev_out must hold 2^len(phys_bits) doubles on the device)."""
+    q = np.ascontiguousarray(phys_bits, dtype=np.int32)
+    _check(load().qs_probs_noalloc(ctypes.c_void_p(dev_amps), n, dtype,
+                                   q.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(q),
+                                   ctypes.c_void_p(dev_out), _stream_handle(stream)))
 
 
 def qs_norm(st):

@@ -19,6 +19,8 @@
 // Control bits never enter the index space: only the 2^(n - controls)
 // amplitudes whose control bits are 1 are read and written.
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "kernels_common.cuh"
 
@@ -386,3 +388,92 @@ cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int
 }
 
 }  // namespace qs
+
+// ---------------------------------------------------------------------------
+// Marginal probabilities without any allocation
+// ---------------------------------------------------------------------------
+// Some callers cannot let a library call cudaMalloc: a serving process that
+// reserved all of its device memory up front through its own pool, or a
+// caller that must not risk the device-wide synchronisation cudaMalloc and
+// cudaFree may imply. For them the per-CTA partial histograms of the
+// probability reduction live in this fixed array instead of state-owned
+// scratch. Every GPU that loads the library keeps these 4 MiB until exit.
+namespace qs {
+std::string &last_error_ref();
+}
+
+namespace {
+
+constexpr int kNoAllocScratchDoubles = 1 << 19;  // 4 MiB
+static __device__ __align__(256) double g_probs_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+qs_status noalloc_fail(qs_status s, const char *msg) {
+  qs::last_error_ref() = msg;
+  return s;
+}
+
+}  // namespace
+
+extern "C" qs_status qs_probs_noalloc(const void *dev_amps, int n, qs_dtype dtype, const int *phys_bits, int m,
+                                      double *dev_out, void *cuda_stream) {
+  using namespace qs;
+  using namespace qs::kern;
+  if (!dev_amps || !dev_out || (m > 0 && !phys_bits))
+    return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: null argument");
+  if (dtype != QS_C64 && dtype != QS_C128) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: unknown dtype");
+  const int nmax = dtype == QS_C64 ? QS_MAX_N_C64 : QS_MAX_N_C128;
+  if (n < 1 || n > nmax) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: qubit count out of range");
+  if (m < 0 || m > n || m > kProbsSmemBits)
+    return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: m must be in 0..min(n, 12)");
+  if (((uintptr_t)dev_amps & 15) != 0 || ((uintptr_t)dev_out & 7) != 0)
+    return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: misaligned device pointer");
+  int pos[kMaxProbBits];
+  for (int j = 0; j < m; j++) {
+    if (phys_bits[j] < 0 || phys_bits[j] >= n) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: bit out of range");
+    for (int i = 0; i < j; i++)
+      if (phys_bits[i] == phys_bits[j]) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: duplicate bit");
+    pos[j] = phys_bits[j];
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return noalloc_fail(QS_ECUDA, "qs_probs_noalloc: cudaGetDevice failed");
+  if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(QS_EUNSUPPORTED, "qs_probs_noalloc: device ordinal too large");
+  double *scratch = nullptr;
+  {
+    // first call on this device: resolve the array's device address once,
+    // with the device current (the host-side name is only a stand-in)
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void *addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_probs_scratch);
+      if (e != cudaSuccess || !addr) return noalloc_fail(QS_ECUDA, "qs_probs_noalloc: cudaGetSymbolAddress failed");
+      g_scratch_ptr[dev] = (double *)addr;
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  ProbsParam p;
+  p.n_amps = 1ll << n;
+  p.m = m;
+  for (int j = 0; j < m; j++) p.pos[j] = pos[j];
+  // every partial slot the reduce kernel reads is written by this call, so
+  // nothing in the array has to start at zero
+  int grid = probs_grid(n);
+  const int cap = kNoAllocScratchDoubles >> m;
+  if (grid > cap) grid = cap;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t smem = sizeof(double) << m;
+  if (dtype == QS_C128) k_probs<double2><<<grid, 256, smem, s>>>((const double2 *)dev_amps, p, scratch);
+  else k_probs<float2><<<grid, 256, smem, s>>>((const float2 *)dev_amps, p, scratch);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const int nb = 1 << m;
+    k_probs_reduce<<<(nb + 255) / 256, 256, 0, s>>>(scratch, grid, nb, dev_out);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) return noalloc_fail(QS_ECUDA, "qs_probs_noalloc: launch failed");
+  return QS_OK;
+}
