@@ -372,6 +372,8 @@ def run_case(args):
     k = {"tc5": 5, "tc4": 4, "dense3": 3}.get(args.case, 0)
     if k:
         qubits = [1, 6, 11, 16, 21][:k] if n > 21 else list(range(0, 2 * k, 2))
+        if args.targets:
+            qubits = [int(x) for x in args.targets.split(",")]
         gates = [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
         gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
         flags = qs.QS_FUSE | qs.QS_FUSE_K(k) | (qs.QS_TC if args.case.startswith("tc") else 0)
@@ -411,6 +413,7 @@ def main():
     ap.add_argument("--case", choices=CASES, help="profiling aid: launch one kernel kind only")
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
     args = ap.parse_args()
     if args.case:
         run_case(args)

@@ -103,6 +103,7 @@ typedef struct {
   double reloc_share;   /* relocate a high qubit carrying >= this share of block time */
   int diag_max;         /* widest diagonal block, 1..QS_MAX_DIAG */
   int threads;          /* launch override: threads per CTA (0 = tuned default) */
+  double peak_gbs;      /* HBM copy bandwidth the cost model scales its priors by */
   int reserved[6];
 } qs_opts;
 
@@ -205,8 +206,37 @@ typedef struct {
 qs_status qs_profile(qs_state *st, qs_profile_summary *out, qs_block_record *recs, size_t cap,
                      size_t *n_recs);
 
-/* Clears the counters and records (start of a new profiling run). */
+/* Clears the counters, records and class table (start of a new profiling run). */
 qs_status qs_profile_reset(qs_state *st);
+
+/*
+ * Measured profile as a throughput table: bytes, device time and launch count
+ * of every profiled block so far, by kernel class
+ *   class = kind * 8 + min(k, 7) + 32 * (tensor cores) + 64 * (a dense
+ *           block whose targets include bits 0 and 1),
+ * kind 0 dense, 1 diagonal, 2 exchange.
+ */
+#define QS_N_CLASSES 128
+typedef struct {
+  double bytes[QS_N_CLASSES];
+  double ms[QS_N_CLASSES];
+  int64_t count[QS_N_CLASSES];
+} qs_class_table;
+
+qs_status qs_profile_classes(const qs_state *st, qs_class_table *out);
+
+/*
+ * Measured-profile activator (the mapping from profile to flags that the
+ * paper leaves open, Sec. III-A). Plans every candidate flag set {plain,
+ * virtual swap, fusion k = 1..6 with diagonal runs, tensor cores for k >= 4}
+ * on the host and predicts its time as the sum over blocks of bytes / class
+ * throughput from `table` (NULL = compiled-in GB300 priors only, scaled to
+ * opts->peak_gbs). Host only; returns the fastest candidate's flags and its
+ * predicted milliseconds. qs_apply_circuit with QS_PGO_MEASURED does the
+ * same with the state's own table and profiles the run it launches.
+ */
+qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates, const qs_class_table *table,
+                        const qs_opts *opts, uint64_t *flags_out, double *predicted_ms);
 
 /*
  * The host passes alone (virtual swap, fusion, classification), without a

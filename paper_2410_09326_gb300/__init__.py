@@ -35,6 +35,7 @@ def QS_FUSE_K(k):
 
 
 QS_N_GATE_TYPES = 33
+QS_N_CLASSES = 128
 QS_MAX_QUBITS = 40
 QS_MAX_DIAG = 10
 
@@ -56,7 +57,12 @@ class qs_opts(ctypes.Structure):
     _fields_ = [("merge_run", ctypes.c_int), ("t_ratio", ctypes.c_double),
                 ("low_bits", ctypes.c_int), ("reloc_share", ctypes.c_double),
                 ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("peak_gbs", ctypes.c_double), ("reserved", ctypes.c_int * 6)]
+
+
+class qs_class_table(ctypes.Structure):
+    _fields_ = [("bytes", ctypes.c_double * QS_N_CLASSES), ("ms", ctypes.c_double * QS_N_CLASSES),
+                ("count", ctypes.c_int64 * QS_N_CLASSES)]
 
 
 class qs_block_record(ctypes.Structure):
@@ -106,6 +112,10 @@ def load(build_if_missing=False):
         "qs_profile": (ctypes.c_int, [vp, ctypes.POINTER(qs_profile_summary),
                                       ctypes.POINTER(qs_block_record), sz, ctypes.POINTER(sz)]),
         "qs_profile_reset": (ctypes.c_int, [vp]),
+        "qs_profile_classes": (ctypes.c_int, [vp, ctypes.POINTER(qs_class_table)]),
+        "qs_pgo_select": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, sz, ctypes.POINTER(qs_class_table),
+                                         ctypes.POINTER(qs_opts), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_double)]),
         "qs_get_perm": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int8)]),
         "qs_measure_probs": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double)]),
@@ -202,6 +212,24 @@ def qs_profile(st, with_records=True):
         _check(lib.qs_profile(st, ctypes.byref(s), arr, n.value, ctypes.byref(n)))
         recs = list(arr)
     return s, recs
+
+
+def qs_profile_classes(st):
+    t = qs_class_table()
+    _check(load().qs_profile_classes(st, ctypes.byref(t)))
+    return t
+
+
+def qs_pgo_select(n, gates, dtype=QS_C64, table=None, opts=None):
+    """Host-only measured-profile activator: returns (flags, predicted_ms)."""
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    f = ctypes.c_uint64(0)
+    ms = ctypes.c_double(0)
+    _check(load().qs_pgo_select(n, dtype, gates.ctypes.data_as(ctypes.c_void_p), gates.size,
+                                ctypes.byref(table) if table is not None else None,
+                                ctypes.byref(opts) if opts is not None else None, ctypes.byref(f),
+                                ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def qs_profile_reset(st):

@@ -61,7 +61,9 @@ def _compile(src, verbose):
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
     else:
-        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", "-Wno-unused-function",
+        # -fcx-limited-range: plain complex products (gate entries are finite)
+        cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-fcx-limited-range", "-pthread", "-Wall",
+               "-Wno-unused-function",
                "-I", INC, "-I", SRC, "-I", os.path.join(cuda, "include"), "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -83,7 +85,8 @@ def build(force=False, verbose=False):
                 sys.stderr.write(log)
     nvcc = os.path.join(_cuda_home(), "bin", "nvcc")
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp] + [o for o, _ in results]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-Xcompiler", "-pthread", "-o", tmp] + \
+        [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -52,6 +52,8 @@ struct qs_state {
   uint64_t flags_used = 0;
   PlanStats last_stats;
   double h2d_bytes = 0;
+  std::vector<int> rec_class;  // kernel class of each record (measured-profile table)
+  qs_class_table classes = {};
 };
 
 namespace {
@@ -82,6 +84,35 @@ qs_status check_device_error(qs_state *st) {
   }
   return QS_OK;
 }
+
+// Resolves the CUDA-event times of the last apply call's blocks (waiting for
+// them when `wait`) and adds them to the per-class throughput table once.
+qs_status resolve_records(qs_state *st, bool wait) {
+  if (!st->recs_timed || st->recs_resolved || st->recs.empty()) return QS_OK;
+  cudaEvent_t last = st->events[st->recs.size()];
+  if (!wait && cudaEventQuery(last) != cudaSuccess) {
+    cudaGetLastError();  // not ready is not an error
+    return QS_OK;
+  }
+  cudaError_t e = cudaEventSynchronize(last);
+  if (e != cudaSuccess) return QS_ECUDA;
+  for (size_t i = 0; i < st->recs.size(); i++) {
+    float t0 = 0, dt = 0;
+    e = cudaEventElapsedTime(&t0, st->events[0], st->events[i]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&dt, st->events[i], st->events[i + 1]);
+    if (e != cudaSuccess) return QS_ECUDA;
+    st->recs[i].t_start_ms = t0;
+    st->recs[i].ms = dt;
+    const int c = st->rec_class[i];
+    st->classes.bytes[c] += st->recs[i].bytes;
+    st->classes.ms[c] += dt;
+    st->classes.count[c] += 1;
+  }
+  st->recs_resolved = true;
+  return QS_OK;
+}
+
+qs_status fold_records(qs_state *st, bool wait) { return resolve_records(st, wait); }
 
 qs_status check_state(const qs_state *st) {
   if (!st) return fail(QS_EINVAL, "null state");
@@ -144,39 +175,6 @@ void record_counters(qs_state *st, const qs_gate *gates, size_t n_gates) {
   st->gates_seen += (int64_t)n_gates;
 }
 
-// Rule-based activator (Sec. III-A "PGO compilation flow", Sec. III-D):
-// one decision per optimisation from the counters of the circuit at hand.
-uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts &o, uint64_t base) {
-  int run[QS_MAX_QUBITS] = {0}, max_run = 0;
-  int64_t swaps = 0, two_q_low = 0, t_count = 0, dense = 0;
-  for (size_t i = 0; i < n_gates; i++) {
-    const qs_gate &g = gates[i];
-    if (g.op == QS_SWAP) swaps++;
-    if (g.op == QS_T || g.op == QS_TDG) t_count++;
-    if (!op_info(g.op).diagonal) dense++;
-    if (g.nq == 1) {
-      max_run = std::max(max_run, ++run[g.q[0]]);
-    } else {
-      for (int j = 0; j < g.nq; j++) run[g.q[j]] = 0;
-      if ((g.op == QS_CX || g.op == QS_CPHASE || g.op == QS_CU1 || g.op == QS_CZ) &&
-          (g.q[g.nq - 1] < o.low_bits))
-        two_q_low++;
-    }
-  }
-  (void)n;
-  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | (15ull << 16));
-  // virtual swap: SWAP gates present, or two-qubit gates hitting the fast
-  // segment (the paper's CPhase/CNOT counter rule)
-  if (swaps > 0 || two_q_low > 0) f |= QS_VSWAP;
-  // merging: a run of consecutive one-qubit gates above the threshold, or
-  // (GPU reading) any circuit with more than one gate, since each fused gate
-  // saves a full pass over the state
-  if (max_run > o.merge_run || n_gates > 1) f |= QS_FUSE | QS_FUSE_K(5) | QS_DIAG | QS_TC;
-  (void)t_count;
-  (void)dense;
-  return f;
-}
-
 }  // namespace
 
 extern "C" {
@@ -190,6 +188,7 @@ void qs_default_opts(qs_opts *o) {
   o->reloc_share = 0.25;
   o->diag_max = QS_MAX_DIAG;
   o->threads = 0;
+  o->peak_gbs = 6688.8;
 }
 
 const char *qs_last_error(void) { return last_error_ref().c_str(); }
@@ -270,7 +269,18 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   if (opts) o = *opts;
   else qs_default_opts(&o);
   DeviceGuard dg(st->device);
-  if (flags & QS_PGO_RULES) flags = rules_select(st->n, gates, n_gates, o, flags);
+  // fold the timings of an earlier profiled call that has finished
+  fold_records(st, false);
+  if (flags & QS_PGO_MEASURED) {
+    std::string err;
+    uint64_t f = 0;
+    s = measured_select(st->n, st->dtype == QS_C128, gates, n_gates, o, &st->classes, flags, &f, nullptr, err);
+    if (s != QS_OK) return fail(s, "qs_apply_circuit: " + err);
+    // a first call has no measurements yet: profile it so the next one has
+    flags = f | QS_PROFILE;
+  } else if (flags & QS_PGO_RULES) {
+    flags = rules_select(st->n, gates, n_gates, o, flags);
+  }
 
   std::vector<Block> plan;
   PlanStats stats;
@@ -321,8 +331,9 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
       st->d_mats = dm;
       st->mats_cap = mat_bytes;
     }
-    for (size_t i = 0; i < plan.size(); i++)
+    parallel_blocks(plan.size(), [&](size_t i) {
       if (mat_off[i] != (size_t)-1) fill_dev_matrix(plan[i], c128, (unsigned char *)st->h_mats + mat_off[i]);
+    });
     e = cudaMemcpyAsync(st->d_mats, st->h_mats, mat_bytes, cudaMemcpyHostToDevice, st->stream);
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
     e = cudaEventRecord(st->mats_copied, st->stream);
@@ -346,6 +357,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
   }
   st->recs.clear();
+  st->rec_class.clear();
   st->recs.reserve(plan.size());
   st->h2d_bytes = 0;
   for (size_t i = 0; i < plan.size(); i++) {
@@ -370,6 +382,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
     r.n_gates = b.n_gates;
       r.cmask = b.cmask;
     r.bytes = block_bytes(b, st->n, ab);
+    st->rec_class.push_back(block_class(b));
     st->h2d_bytes += (double)block_param_bytes(b, c128);
     r.t_start_ms = -1;
     r.ms = -1;
@@ -389,19 +402,7 @@ qs_status qs_profile(qs_state *st, qs_profile_summary *out, qs_block_record *rec
   if (s != QS_OK) return s;
   if (!out) return fail(QS_EINVAL, "null summary");
   DeviceGuard dg(st->device);
-  if (st->recs_timed && !st->recs_resolved && !st->recs.empty()) {
-    cudaError_t e = cudaEventSynchronize(st->events[st->recs.size()]);
-    if (e != cudaSuccess) return cuda_fail(st, e, "qs_profile");
-    for (size_t i = 0; i < st->recs.size(); i++) {
-      float a = 0, b = 0;
-      e = cudaEventElapsedTime(&a, st->events[0], st->events[i]);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, st->events[i], st->events[i + 1]);
-      if (e != cudaSuccess) return cuda_fail(st, e, "qs_profile");
-      st->recs[i].t_start_ms = a;
-      st->recs[i].ms = b;
-    }
-    st->recs_resolved = true;
-  }
+  if (resolve_records(st, true) != QS_OK) return cuda_fail(st, cudaGetLastError(), "qs_profile");
   std::memset(out, 0, sizeof(*out));
   out->n_qubits = st->n;
   out->n_blocks = (int)st->recs.size();
@@ -427,8 +428,29 @@ qs_status qs_profile(qs_state *st, qs_profile_summary *out, qs_block_record *rec
   return QS_OK;
 }
 
+qs_status qs_profile_classes(const qs_state *st, qs_class_table *out) {
+  if (!st || !out) return fail(QS_EINVAL, "null argument");
+  *out = st->classes;
+  return QS_OK;
+}
+
+qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates, const qs_class_table *table,
+                        const qs_opts *opts, uint64_t *flags_out, double *predicted_ms) {
+  if (!flags_out || (n_gates && !gates)) return fail(QS_EINVAL, "null argument");
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qubit count out of range");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  qs_opts o;
+  if (opts) o = *opts;
+  else qs_default_opts(&o);
+  std::string err;
+  qs_status s = measured_select(n, dtype == QS_C128, gates, n_gates, o, table, 0, flags_out, predicted_ms, err);
+  if (s != QS_OK) return fail(s, "qs_pgo_select: " + err);
+  return QS_OK;
+}
+
 qs_status qs_profile_reset(qs_state *st) {
   if (!st) return fail(QS_EINVAL, "null state");
+  std::memset(&st->classes, 0, sizeof(st->classes));
   std::memset(st->counters, 0, sizeof(st->counters));
   std::memset(st->run_1q, 0, sizeof(st->run_1q));
   std::memset(st->max_run_1q, 0, sizeof(st->max_run_1q));

@@ -27,6 +27,26 @@
 namespace qs {
 namespace kern {
 
+int resident_ctas(const void *func, int threads, size_t dyn_smem) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int regs_sm = 65536, smem_sm = 228 * 1024, thr_sm = 2048, reserved = 1024;
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;  // 256-register allocation units
+  int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * warps) : 64;
+  int by_smem = (int)(smem_sm / (fa.sharedSizeBytes + dyn_smem + reserved));
+  int by_thr = thr_sm / threads;
+  int r = by_regs < by_smem ? by_regs : by_smem;
+  if (by_thr < r) r = by_thr;
+  return r < 1 ? 1 : r;
+}
+
 int grid_for(long long work, int threads) {
   const DevInfo &di = dev_info();
   long long want = (work + threads - 1) / threads;
@@ -163,29 +183,52 @@ __device__ __forceinline__ int extract_bits(uint64_t i, const int *pos, int m) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_probs(const T *__restrict__ a, const __grid_constant__ ProbsParam p,
                                                double *__restrict__ partial) {
+  // each thread keeps UNROLL 16-byte loads in flight per trip (two complex64
+  // amplitudes or one complex128 amplitude per load)
+  constexpr int PER = sizeof(T) == 8 ? 2 : 1;
+  constexpr int UNROLL = 4;
   extern __shared__ double hist[];
   const int nb = 1 << p.m;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) hist[i] = 0.0;
   __syncthreads();
   const unsigned lane = threadIdx.x & 31;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long n_vec = p.n_amps / PER;
+  const long long S = (long long)gridDim.x * blockDim.x;
   // every lane runs the same trip count so the warp collectives stay converged
-  const long long trips = (p.n_amps + stride - 1) / stride;
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  for (long long t = 0; t < trips; t++, i += stride) {
-    double v = 0.0;
-    int b = 0;
-    if (i < p.n_amps) {
-      const T x = a[i];
-      v = (double)x.x * (double)x.x + (double)x.y * (double)x.y;
-      b = extract_bits((uint64_t)i, p.pos, p.m);
+  const long long trips = (n_vec + S * UNROLL - 1) / (S * UNROLL);
+  const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long t = 0; t < trips; t++) {
+    double v[UNROLL * PER];
+    int bin[UNROLL * PER];
+#pragma unroll
+    for (int u = 0; u < UNROLL; u++) {
+      const long long j = j0 + (t * UNROLL + u) * S;
+      if (j < n_vec) {
+        if constexpr (PER == 2) {
+          const float4 x = *reinterpret_cast<const float4 *>(a + 2 * j);
+          v[2 * u] = (double)x.x * x.x + (double)x.y * x.y;
+          v[2 * u + 1] = (double)x.z * x.z + (double)x.w * x.w;
+        } else {
+          const T x = a[j];
+          v[u] = (double)x.x * x.x + (double)x.y * x.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < PER; e++) v[u * PER + e] = 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < PER; e++) bin[u * PER + e] = extract_bits((uint64_t)(j * PER + e), p.pos, p.m);
     }
-    const int b0 = __shfl_sync(0xffffffffu, b, 0);
-    if (__all_sync(0xffffffffu, b == b0)) {
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && v != 0.0) atomicAdd(&hist[b0], v);
-    } else if (v != 0.0) {
-      atomicAdd(&hist[b], v);
+#pragma unroll
+    for (int e = 0; e < UNROLL * PER; e++) {
+      const int b0 = __shfl_sync(0xffffffffu, bin[e], 0);
+      if (__all_sync(0xffffffffu, bin[e] == b0)) {
+        double s = v[e];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s != 0.0) atomicAdd(&hist[b0], s);
+      } else if (v[e] != 0.0) {
+        atomicAdd(&hist[bin[e]], v[e]);
+      }
     }
   }
   __syncthreads();
@@ -316,6 +359,168 @@ cudaError_t launch_block(void *amps, int n, bool c128, const Block &b, cudaStrea
   return launch_block_with_matrix(amps, n, c128, b, nullptr, nullptr, s, threads);
 }
 
+// Marginals with more than 12 measured bits. The state is cut into chunks
+// of 2^12 contiguous amplitudes; within a chunk the measured bits above bit
+// 11 are constant (they give the high part of the bin) and the measured bits
+// below bit 12 index a shared-memory sub-histogram. Chunks are visited in an
+// order whose fastest-varying bits are the summed-out high bits, so a CTA
+// walking a contiguous range of that order flushes its sub-histogram (FP64
+// global atomics into the zeroed output) only when the high part changes.
+constexpr int kProbChunkBits = 12;
+
+struct ProbsChunkParam {
+  int m_lo;                      // measured bits below kProbChunkBits
+  int lo_pos[kProbChunkBits];    // their positions
+  int lo_j[kProbChunkBits];      // their bin bit
+  int n_sum_hi;                  // summed-out bits >= kProbChunkBits
+  int sum_hi_pos[64];
+  int m_hi;                      // measured bits >= kProbChunkBits
+  int hi_pos[kMaxProbBits];
+  int hi_j[kMaxProbBits];
+  long long n_chunks;
+};
+
+__device__ __forceinline__ void chunk_of(long long cp, const ProbsChunkParam &p, uint64_t &chunk_base,
+                                         unsigned &hi_bin) {
+  // cp = (measured-high bits, summed-high bits fastest) -> amplitude index of
+  // the chunk start and the high part of its bin
+  uint64_t base = 0;
+  int b = 0;
+  for (int i = 0; i < p.n_sum_hi; i++, b++) base |= (uint64_t)((cp >> b) & 1) << p.sum_hi_pos[i];
+  unsigned hb = 0;
+  for (int i = 0; i < p.m_hi; i++, b++) {
+    const unsigned bit = (unsigned)((cp >> b) & 1);
+    base |= (uint64_t)bit << p.hi_pos[i];
+    hb |= bit << p.hi_j[i];
+  }
+  chunk_base = base;
+  hi_bin = hb;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_probs_chunk(const T *__restrict__ a, const __grid_constant__ ProbsChunkParam p,
+                                                     double *__restrict__ out) {
+  // Thread t always reads the same NSLOT offsets of every chunk, so the low
+  // part of each slot's bin never changes: the squares accumulate in
+  // registers and meet (warp reduction, shared histogram, FP64 atomics into
+  // `out`) only when the chunk's high part of the bin changes.
+  constexpr int CH = 1 << kProbChunkBits;
+  constexpr int PER = sizeof(T) == 8 ? 2 : 1;  // amplitudes per 16-byte load
+  constexpr int NLD = CH / (256 * PER);        // loads per thread per chunk
+  constexpr int NSLOT = NLD * PER;
+  __shared__ double hist[CH];
+  const int nsub = 1 << p.m_lo;
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) hist[s] = 0.0;
+  int sub[NSLOT];
+#pragma unroll
+  for (int u = 0; u < NLD; u++)
+#pragma unroll
+    for (int e = 0; e < PER; e++) {
+      const int o = (threadIdx.x + u * 256) * PER + e;
+      int s = 0;
+      for (int i = 0; i < p.m_lo; i++) s |= ((o >> p.lo_pos[i]) & 1) << i;
+      sub[u * PER + e] = s;
+    }
+  auto lo_bin = [&](int s) {
+    unsigned b = 0;
+    for (int i = 0; i < p.m_lo; i++) b |= (unsigned)((s >> i) & 1) << p.lo_j[i];
+    return b;
+  };
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31;
+  // complex64: each slot sums |a|^2 in compensated FP32 (Kahan) and meets
+  // FP64 at the flush; GB300's FP64 rate could not keep up with one FP64
+  // operation per amplitude at HBM speed. complex128: FP64 throughout.
+  using Acc = typename Real<T>::type;
+  Acc acc[NSLOT], comp[NSLOT];
+#pragma unroll
+  for (int e = 0; e < NSLOT; e++) acc[e] = comp[e] = 0;
+  // when every slot of every thread in the CTA lands in the same bin (no
+  // measured bit below bit 12), the slots are summed in the thread first
+  bool same = true;
+#pragma unroll
+  for (int e = 1; e < NSLOT; e++) same &= sub[e] == sub[0];
+  const bool one_bin = __syncthreads_and(same && sub[0] == 0);
+  auto flush = [&](unsigned hb) {
+    if (one_bin) {
+      double v = 0.0;
+#pragma unroll
+      for (int e = 0; e < NSLOT; e++) {
+        v += (double)acc[e] - (double)comp[e];
+        acc[e] = comp[e] = 0;
+      }
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0 && v != 0.0) atomicAdd(&hist[0], v);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (hist[0] != 0.0) atomicAdd(&out[hb], hist[0]);
+        hist[0] = 0.0;
+      }
+      __syncthreads();
+      return;
+    }
+#pragma unroll
+    for (int e = 0; e < NSLOT; e++) {
+      const int b0 = __shfl_sync(0xffffffffu, sub[e], 0);
+      double v = (double)acc[e] - (double)comp[e];
+      acc[e] = comp[e] = 0;
+      if (__all_sync(0xffffffffu, sub[e] == b0)) {
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0 && v != 0.0) atomicAdd(&hist[b0], v);
+      } else if (v != 0.0) {
+        atomicAdd(&hist[sub[e]], v);
+      }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+      const double v = hist[s];
+      if (v != 0.0) atomicAdd(&out[hb | lo_bin(s)], v);
+      hist[s] = 0.0;
+    }
+    __syncthreads();
+  };
+  // contiguous range of the chunk order for this CTA
+  const long long per = (p.n_chunks + gridDim.x - 1) / gridDim.x;
+  const long long c0 = (long long)blockIdx.x * per;
+  const long long c1 = c0 + per < p.n_chunks ? c0 + per : p.n_chunks;
+  unsigned cur_hi = 0;
+  bool dirty = false;
+  for (long long cp = c0; cp < c1; cp++) {
+    uint64_t base;
+    unsigned hb;
+    chunk_of(cp, p, base, hb);
+    if (dirty && hb != cur_hi) flush(cur_hi);
+    cur_hi = hb;
+    dirty = true;
+    T xs[NSLOT];
+#pragma unroll
+    for (int u = 0; u < NLD; u++) {
+      const int o = (threadIdx.x + u * 256) * PER;
+      if constexpr (PER == 2) {
+        const float4 x = *reinterpret_cast<const float4 *>(a + base + o);
+        xs[2 * u].x = x.x;
+        xs[2 * u].y = x.y;
+        xs[2 * u + 1].x = x.z;
+        xs[2 * u + 1].y = x.w;
+      } else {
+        xs[u] = a[base + o];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < NSLOT; e++) {
+      if constexpr (sizeof(T) == 8) {
+        const float y = fmaf(xs[e].x, xs[e].x, xs[e].y * xs[e].y) - comp[e];
+        const float t = acc[e] + y;
+        comp[e] = (t - acc[e]) - y;
+        acc[e] = t;
+      } else {
+        acc[e] += xs[e].x * xs[e].x + xs[e].y * xs[e].y;
+      }
+    }
+  }
+  if (__syncthreads_or(dirty)) flush(cur_hi);
+}
+
 template <typename T> size_t param_bytes_t(const Block &b) {
   if (b.kind == BK_PERMUTE) return sizeof(T *) + sizeof(long long) + 2 * sizeof(int);
   if (b.kind == BK_DIAG) return sizeof(T *) + sizeof(DiagParam<T>);
@@ -358,7 +563,7 @@ int probs_grid(int n) {
 }
 
 size_t probs_scratch_doubles(int n, int m) {
-  if (m > kProbsSmemBits) return 0;
+  if (m > kProbsSmemBits || n >= kProbChunkBits) return 0;
   return (size_t)probs_grid(n) << m;
 }
 
@@ -369,7 +574,7 @@ cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int
   p.n_amps = 1ll << n;
   p.m = m;
   for (int j = 0; j < m; j++) p.pos[j] = pos[j];
-  if (m <= kProbsSmemBits) {
+  if (m <= kProbsSmemBits && n < kProbChunkBits) {
     const int grid = probs_grid(n);
     const size_t smem = sizeof(double) << m;
     if (c128) k_probs<double2><<<grid, 256, smem, s>>>((const double2 *)amps, p, partial);
@@ -381,6 +586,40 @@ cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int
     return cudaGetLastError();
   }
   const long long nb = 1ll << m;
+  if (n >= kProbChunkBits) {
+    ProbsChunkParam c;
+    std::memset(&c, 0, sizeof(c));
+    bool used[64] = {false};
+    for (int j = 0; j < m; j++) {
+      used[pos[j]] = true;
+      if (pos[j] < kProbChunkBits) {
+        c.lo_pos[c.m_lo] = pos[j];
+        c.lo_j[c.m_lo++] = j;
+      }
+    }
+    for (int q = kProbChunkBits; q < n; q++) {
+      if (used[q]) continue;
+      c.sum_hi_pos[c.n_sum_hi++] = q;
+    }
+    // measured high bits in ascending position order
+    for (int q = kProbChunkBits; q < n; q++)
+      for (int j = 0; j < m; j++)
+        if (pos[j] == q) {
+          c.hi_pos[c.m_hi] = q;
+          c.hi_j[c.m_hi++] = j;
+        }
+    c.n_chunks = 1ll << (n - kProbChunkBits);
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nb, s);
+    if (e != cudaSuccess) return e;
+    // one wave of resident CTAs
+    const int occ = c128 ? resident_ctas((const void *)k_probs_chunk<double2>, 256, 0)
+                         : resident_ctas((const void *)k_probs_chunk<float2>, 256, 0);
+    long long grid = (long long)dev_info().sms * occ;
+    if (grid > c.n_chunks) grid = c.n_chunks;
+    if (c128) k_probs_chunk<double2><<<(int)grid, 256, 0, s>>>((const double2 *)amps, c, out);
+    else k_probs_chunk<float2><<<(int)grid, 256, 0, s>>>((const float2 *)amps, c, out);
+    return cudaGetLastError();
+  }
   const int grid = grid_for(nb, 256);
   if (c128) k_probs_wide<double2><<<grid, 256, 0, s>>>((const double2 *)amps, p, n, out);
   else k_probs_wide<float2><<<grid, 256, 0, s>>>((const float2 *)amps, p, n, out);

@@ -37,24 +37,41 @@ struct DenseIdx {
   int tq[QS_MAX_FUSE];
 };
 
-template <typename T, int K>
+template <typename T, int K, bool PAIR = false>
 __device__ __forceinline__ void group_apply(T *__restrict__ a, uint64_t base, const uint64_t *d,
                                             const T *m) {
   using R = typename Real<T>::type;
   constexpr int D = 1 << K;
   T v[D];
+  if constexpr (PAIR) {
+    // bit 0 is a target (complex64): elements s and s+1 share one 16-byte access
 #pragma unroll
-  for (int s = 0; s < D; s++) {
-    uint64_t off = 0;
+    for (int s = 0; s < D; s += 2) {
+      uint64_t off = 0;
 #pragma unroll
-    for (int j = 0; j < K; j++)
-      if ((s >> j) & 1) off += d[j];
-    v[s] = a[base + off];
+      for (int j = 1; j < K; j++)
+        if ((s >> j) & 1) off += d[j];
+      const float4 x = *reinterpret_cast<const float4 *>(a + base + off);
+      v[s].x = x.x;
+      v[s].y = x.y;
+      v[s + 1].x = x.z;
+      v[s + 1].y = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < D; s++) {
+      uint64_t off = 0;
+#pragma unroll
+      for (int j = 0; j < K; j++)
+        if ((s >> j) & 1) off += d[j];
+      v[s] = a[base + off];
+    }
   }
   // The store addresses are recomputed from an opaque copy of the base
   // instead of keeping 2^K 64-bit load addresses live across the mat-vec.
   uint64_t base2 = base;
   asm volatile("" : "+l"(base2));
+  T y[2];
 #pragma unroll
   for (int r = 0; r < D; r++) {
     R re = 0, im = 0;
@@ -66,14 +83,23 @@ __device__ __forceinline__ void group_apply(T *__restrict__ a, uint64_t base, co
       im = fma(w.x, v[c].y, im);
       im = fma(w.y, v[c].x, im);
     }
-    uint64_t off = 0;
+    y[r & 1].x = re;
+    y[r & 1].y = im;
+    if constexpr (PAIR) {
+      if (r & 1) {
+        uint64_t off = 0;
 #pragma unroll
-    for (int j = 0; j < K; j++)
-      if ((r >> j) & 1) off += d[j];
-    T y;
-    y.x = re;
-    y.y = im;
-    a[base2 + off] = y;
+        for (int j = 1; j < K; j++)
+          if ((r >> j) & 1) off += d[j];
+        *reinterpret_cast<float4 *>(a + base2 + off) = make_float4(y[0].x, y[0].y, y[1].x, y[1].y);
+      }
+    } else {
+      uint64_t off = 0;
+#pragma unroll
+      for (int j = 0; j < K; j++)
+        if ((r >> j) & 1) off += d[j];
+      a[base2 + off] = y[r & 1];
+    }
   }
 }
 
@@ -92,6 +118,13 @@ __global__ void __launch_bounds__(256, DenseOcc<T, K>::value) k_dense_param(T *_
 #pragma unroll
   for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
   const long long stride = (long long)gridDim.x * blockDim.x;
+  if (sizeof(T) == 8 && K >= 1 && p.tq[0] == 0) {
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < p.n_groups; g += stride) {
+      const uint64_t base = insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask;
+      group_apply<T, K, sizeof(T) == 8>(a, base, d, p.m);
+    }
+    return;
+  }
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < p.n_groups; g += stride) {
     const uint64_t base = insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask;
     group_apply<T, K>(a, base, d, p.m);
@@ -118,6 +151,8 @@ __global__ void __launch_bounds__(256, DenseOcc<T, K>::value) k_dense_smem(T *__
 
 
 int grid_for(long long work, int threads);
+// CTAs of `func` that fit on one SM (registers, shared memory, threads).
+int resident_ctas(const void *func, int threads, size_t dyn_smem);
 
 inline void fill_fixed(const Block &b, int *fixed, int &nf) {
   uint64_t m = b.cmask;

@@ -9,8 +9,10 @@
 // QCOR's two-qubit block merging (Sec. IV, "all-on" set) to blocks of up to k
 // qubits whose product matrix is formed in FP64 on the host.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "qs_internal.h"
 
@@ -61,6 +63,25 @@ void left_multiply(std::vector<cd> &M, int w, const std::vector<cd> &G, const in
       }
     }
   }
+}
+
+// Runs f(0..n) on up to 16 host threads when the work is large enough to pay
+// for them (block products are independent once the grouping is fixed).
+template <typename F> void parallel_for(size_t n, F f) {
+  unsigned nt = std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n < 16 || nt <= 1) {
+    for (size_t i = 0; i < n; i++) f(i);
+    return;
+  }
+  if (nt > n / 4) nt = (unsigned)std::max<size_t>(1, n / 4);
+  std::atomic<size_t> next{0};
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (unsigned t = 0; t < nt; t++)
+    th.emplace_back([&] {
+      for (size_t i; (i = next.fetch_add(1)) < n;) f(i);
+    });
+  for (auto &x : th) x.join();
 }
 
 struct Pending {
@@ -199,6 +220,8 @@ bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_p
 
 }  // namespace
 
+void parallel_blocks(size_t n, const std::function<void(size_t)> &f) { parallel_for(n, f); }
+
 double block_bytes(const Block &b, int n, int amp_bytes) {
   double amps = std::ldexp(1.0, n - b.nctrl);
   if (b.kind == BK_PERMUTE) amps = std::ldexp(1.0, n - 1);
@@ -316,12 +339,14 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   }
 
   // (3) products and classification
+  std::vector<Block> done(groups.size());
+  std::vector<char> keep(groups.size(), 0);
+  parallel_for(groups.size(), [&](size_t i) {
+    if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i]) ? 1 : 0;
+  });
   plan.reserve(groups.size());
-  for (const Pending &p : groups) {
-    if (p.members.empty()) continue;
-    Block b;
-    if (finish_block(pg, p, true, b)) plan.push_back(std::move(b));
-  }
+  for (size_t i = 0; i < groups.size(); i++)
+    if (keep[i]) plan.push_back(std::move(done[i]));
   for (Block &b : plan)
     b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= 5;
   return QS_OK;

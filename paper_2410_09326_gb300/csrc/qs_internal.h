@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -71,6 +72,18 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
                      PlanStats &stats, std::string &err);
 
 double block_bytes(const Block &b, int n, int amp_bytes);
+
+// f(0..n) on a few host threads (passes.cpp).
+void parallel_blocks(size_t n, const std::function<void(size_t)> &f);
+
+// Profile-guided selection (pgo.cpp).
+uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts &o, uint64_t base);
+int block_class(const Block &b);
+double predict_plan_ms(const std::vector<Block> &plan, int n, int amp_bytes, const qs_class_table *t,
+                       double peak_gbs);
+qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
+                          const qs_class_table *t, uint64_t base, uint64_t *flags_out, double *pred_ms,
+                          std::string &err);
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels.cu). All asynchronous on `s`.

@@ -135,8 +135,14 @@ struct TcParam {
 
 // K = targets (4 or 5). bmat: B_hi then B_lo, each N x N floats already in
 // the core-matrix layout (built on the host). err: error word (0 = fine).
+// Resident CTAs per SM the register budget is sized for (shared memory
+// allows 4 at K = 4 and 2 at K = 5).
+template <int K> struct TcOcc {
+  static constexpr int value = K <= 4 ? 4 : 2;
+};
+
 template <int K, bool SPLIT, bool RENORM>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, TcOcc<K>::value)
     k_dense_tc(float2 *__restrict__ a, const float4 *__restrict__ bmat, const __grid_constant__ TcParam p,
                int *__restrict__ err) {
   constexpr int D = 1 << K;             // amplitudes per group
@@ -185,6 +191,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t d[K];
 #pragma unroll
   for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
+  const bool pair = p.tq[0] == 0;
   // this thread's row of A: 8-row group (tid / 8), row (tid % 8) of each core matrix
   const uint32_t row_off = (uint32_t)(tid >> 3) * SBO_A + (uint32_t)(tid & 7) * 16u;
   uint32_t phase = 0;
@@ -200,13 +207,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long g = t * kTcThreads + tid;
     ok = t < p.n_tiles && g < p.n_groups;
     b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
+    if (pair) {
+      // bit 0 is a target: elements s and s+1 are adjacent, one 16-byte load
 #pragma unroll
-    for (int s = 0; s < D; s++) {
-      uint64_t off = 0;
+      for (int s = 0; s < D; s += 2) {
+        uint64_t off = 0;
 #pragma unroll
-      for (int j = 0; j < K; j++)
-        if ((s >> j) & 1) off += d[j];
-      v[s] = ok ? a[b + off] : make_float2(0.f, 0.f);
+        for (int j = 1; j < K; j++)
+          if ((s >> j) & 1) off += d[j];
+        const float4 x = ok ? *reinterpret_cast<const float4 *>(a + b + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[s] = make_float2(x.x, x.y);
+        v[s + 1] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < D; s++) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+          if ((s >> j) & 1) off += d[j];
+        v[s] = ok ? a[b + off] : make_float2(0.f, 0.f);
+      }
     }
   };
   gather(tile, base, valid);
@@ -297,13 +318,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int i = 0; i < KR; i++) r[i] = __float_as_uint(__uint_as_float(r[i]) * f);
     }
     if (cur_valid) {
+      if (pair) {
 #pragma unroll
-      for (int s = 0; s < D; s++) {
-        uint64_t off = 0;
+        for (int s = 0; s < D; s += 2) {
+          uint64_t off = 0;
 #pragma unroll
-        for (int j = 0; j < K; j++)
-          if ((s >> j) & 1) off += d[j];
-        a[cur_base + off] = make_float2(__uint_as_float(r[2 * s]), __uint_as_float(r[2 * s + 1]));
+          for (int j = 1; j < K; j++)
+            if ((s >> j) & 1) off += d[j];
+          *reinterpret_cast<float4 *>(a + cur_base + off) =
+              make_float4(__uint_as_float(r[2 * s]), __uint_as_float(r[2 * s + 1]), __uint_as_float(r[2 * s + 2]),
+                          __uint_as_float(r[2 * s + 3]));
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < D; s++) {
+          uint64_t off = 0;
+#pragma unroll
+          for (int j = 0; j < K; j++)
+            if ((s >> j) & 1) off += d[j];
+          a[cur_base + off] = make_float2(__uint_as_float(r[2 * s]), __uint_as_float(r[2 * s + 1]));
+        }
       }
     }
   }
@@ -367,20 +401,21 @@ cudaError_t run_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err
   fill_fixed(b, p.fixed, p.nf);
   for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
   const size_t smem = tc_smem_bytes<K>();
+  // per device: opt in to the shared memory, then size one wave of resident
+  // CTAs (registers and shared memory decide how many; TMEM columns stay
+  // within 512 per SM: at most 4 CTAs x 64 or 2 x 128)
   static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_dense_tc<K, SPLIT, RENORM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc<K, SPLIT, RENORM>, kTcThreads, smem);
+    per_sm = occ > TcOcc<K>::value ? TcOcc<K>::value : occ;
     configured = dev;
   }
-  // resident CTAs per SM: limited by shared memory; TMEM columns stay within
-  // 512 per SM (at most 4 CTAs x 64 columns here)
-  int per_sm = (int)((227 * 1024) / (smem + 1024));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 4) per_sm = 4;
   long long grid = (long long)dev_info().sms * per_sm;
   if (grid > p.n_tiles) grid = p.n_tiles;
   k_dense_tc<K, SPLIT, RENORM><<<(int)grid, kTcThreads, smem, s>>>(a, (const float4 *)dev_b, p, err);

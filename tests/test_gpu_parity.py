@@ -27,6 +27,7 @@ FLAGS = {
     "vswap": qs.QS_VSWAP,
     "diag": qs.QS_DIAG,
     "pgo_rules": qs.QS_PGO_RULES,
+    "pgo_measured": qs.QS_PGO_MEASURED,
     **{f"vswap_k{k}": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) for k in range(1, 7)},
     **{f"vswap_k{k}_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)},
     **{f"vswap_k{k}_tc": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC for k in (4, 5, 6)},
@@ -58,9 +59,13 @@ def check(n, gates, flags, dtype, init=None):
     text = cg.to_qasm(n, gates)
     want, operm = oracle.simulate(text, init=init)
     got, perm = gpu_run(n, qs.gates_to_array(gates), flags, dtype, init=init)
-    if flags & (qs.QS_VSWAP | qs.QS_PGO_RULES) and any(g[0] == "swap" for g in gates):
-        assert list(perm) == list(operm), (list(perm), list(operm))
-    elif not flags & (qs.QS_VSWAP | qs.QS_PGO_RULES):
+    pgo = qs.QS_PGO_RULES | qs.QS_PGO_MEASURED
+    if flags & (qs.QS_VSWAP | pgo) and any(g[0] == "swap" for g in gates):
+        if flags & qs.QS_PGO_MEASURED and list(perm) == list(range(n)):
+            pass  # the measured activator may choose a plan without virtual swap
+        else:
+            assert list(perm) == list(operm), (list(perm), list(operm))
+    elif not flags & (qs.QS_VSWAP | pgo):
         assert list(perm) == list(range(n))
     assert sorted(perm) == list(range(n))
     err = np.linalg.norm(got - oracle.to_physical(want, perm))
@@ -197,6 +202,66 @@ def test_probs_and_norm(dtype):
             got = qs.qs_measure_probs(st, qubits)
             ref = oracle.probs(want, qubits) if qubits else np.array([1.0])
             assert np.abs(got - ref).max() < tol, qubits
+    finally:
+        qs.qs_free_state(st)
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+def test_wide_marginals_n20(dtype):
+    """More than 12 measured qubits: the chunked kernel, low/high/mixed bits."""
+    n = 20
+    rng = cg.SplitMix64(8)
+    gates = cg.random_layered(n, 5, rng, n_swaps=6)
+    want, _ = oracle.simulate(cg.to_qasm(n, gates))
+    st = qs.qs_alloc_state(n, dtype)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k3_diag"])
+        subsets = [list(range(16)), list(range(4, 20)), list(range(19, 3, -1)),
+                   sorted(rng.shuffle(list(range(n)))[:14]), list(range(n))[::-1], list(range(13))]
+        tol = 1e-6 if dtype == qs.QS_C64 else 1e-13
+        for qubits in subsets:
+            got = qs.qs_measure_probs(st, qubits)
+            ref = oracle.probs(want, qubits)
+            assert np.abs(got - ref).max() < tol, (qubits, np.abs(got - ref).max())
+            assert abs(got.sum() - 1) < 10 * tol
+    finally:
+        qs.qs_free_state(st)
+
+
+def test_measured_pgo_regret():
+    """The measured-profile activator, fed by profiled runs of the candidate
+    flag sets on this GPU, picks a set whose measured time is within 15% of
+    the best candidate's (brute force over the same candidates)."""
+    n = 24
+    c = cg.config1_circuits(n=n)
+    _, gates = c["random"]
+    arr = qs.gates_to_array(gates)
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        times = {}
+        cands = [qs.QS_PLAIN, qs.QS_VSWAP] + [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG
+                                             for k in range(1, 7)] + \
+                [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | qs.QS_TC for k in (4, 5, 6)]
+        for f in cands:
+            best = 1e9
+            for _ in range(2):
+                qs.qs_set_basis(st, 0)
+                qs.qs_apply_circuit(st, arr, f | qs.QS_PROFILE)
+                summ, _ = qs.qs_profile(st, with_records=False)
+                best = min(best, summ.total_ms)
+            times[f] = best
+        table = qs.qs_profile_classes(st)
+        chosen, pred = qs.qs_pgo_select(n, arr, table=table)
+        qs.qs_set_basis(st, 0)
+        qs.qs_apply_circuit(st, arr, chosen | qs.QS_PROFILE)
+        summ, _ = qs.qs_profile(st, with_records=False)
+        t_chosen = min(summ.total_ms, times.get(chosen, 1e9))
+        assert t_chosen <= 1.15 * min(times.values()), (hex(chosen), t_chosen, sorted(times.values())[:3])
+        # QS_PGO_MEASURED inside apply uses the same table and stays correct
+        qs.qs_set_basis(st, 0)
+        qs.qs_apply_circuit(st, arr, qs.QS_PGO_MEASURED)
+        summ, _ = qs.qs_profile(st, with_records=False)
+        assert summ.flags_used & qs.QS_FUSE
     finally:
         qs.qs_free_state(st)
 

@@ -231,3 +231,57 @@ def test_swaps_absorbed_count():
     assert recs[1].qubits[0] == 1 and recs[1].nctrl == 1
     recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_PLAIN)
     assert [r.kind for r in recs] == [0, 2, 0, 2]
+
+
+# ---------------------------------------------------------------------------
+# Profile-guided selection (host side)
+# ---------------------------------------------------------------------------
+
+def test_rules_select_follows_the_paper_rules():
+    # a SWAP present -> virtual swap; more than one gate -> fusion
+    n, gates = cg.config0_circuit(0)
+    recs, _, perm = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_PGO_RULES)
+    _, operm = oracle.simulate(cg.to_qasm(n, gates))
+    assert list(perm) == list(operm)  # SWAPs were absorbed
+    assert len(recs) < len(gates) // 2  # and gates were merged
+
+
+def test_measured_select_with_priors_prefers_wide_tensor_core_blocks():
+    c = cg.config1_circuits(n=30)
+    n, gates = c["random"]
+    flags, ms = qs.qs_pgo_select(n, qs.gates_to_array(gates))
+    assert flags & qs.QS_VSWAP and flags & qs.QS_FUSE and flags & qs.QS_TC
+    assert (flags >> 16) & 15 in (4, 5)
+    assert 100 < ms < 5000
+    # GHZ has no SWAP: no virtual swap in the choice
+    n, gates = c["ghz"]
+    flags, _ = qs.qs_pgo_select(n, qs.gates_to_array(gates))
+    assert not flags & qs.QS_VSWAP and flags & qs.QS_FUSE
+
+
+def test_measured_select_follows_the_table():
+    """A table in which every tensor-core class ran slowly steers the choice
+    away from the tensor cores; one in which wide CUDA-core blocks ran fast
+    steers it to them."""
+    c = cg.config1_circuits(n=26)
+    n, gates = c["random"]
+    arr = qs.gates_to_array(gates)
+    t = qs.qs_class_table()
+    for cls in range(qs.QS_N_CLASSES):
+        kind, k, tc = (cls % 32) // 8, cls % 8, bool(cls & 32)
+        gbs = 6000.0
+        if tc:
+            gbs = 300.0
+        elif kind == 0 and k >= 4:
+            gbs = 500.0
+        t.bytes[cls] = gbs * 1e9 * 1e-3  # bytes moved in 1 ms at that rate
+        t.ms[cls] = 1.0
+        t.count[cls] = 1
+    flags, _ = qs.qs_pgo_select(n, arr, table=t)
+    assert not flags & qs.QS_TC and (flags >> 16) & 15 <= 3
+    for cls in range(qs.QS_N_CLASSES):
+        kind, k = (cls % 32) // 8, cls % 8
+        if kind == 0 and k == 6 and not cls & 32:
+            t.bytes[cls] = 7000.0 * 1e6
+    flags, _ = qs.qs_pgo_select(n, arr, table=t)
+    assert (flags >> 16) & 15 == 6 and not flags & qs.QS_TC
