@@ -239,7 +239,7 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     achieved = dbytes / (dms * 1e-3) / 1e9
     traffic = TRAFFIC_PER_LAUNCH.get(dom)
-    launches = len(recs) + args.steps * len(circuits) * 3  # blocks + basis reset + 2 reduction kernels
+    launches = len(recs) + args.steps * len(circuits) * 2  # blocks + basis reset + reduction kernel
 
     if rank != 0:
         qs.qs_free_state(st)
@@ -277,9 +277,10 @@ def run_ours(args):
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of that kernel,
-# scaled to n=30 by the amplitudes processed (profiles/k_dense_tc5_n26.md:
-# 1012.1 MB at n=26 -> x16); None where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {"k_dense_k5_tc": 16.19e9}
+# scaled to n=30 by the amplitudes processed (profiles/k_dense_tc5_n26.md,
+# profiles/k_diag_chunk_n26.md: 1012.3 / 1012.2 MB at n=26 -> x16); absent
+# where no capture of the current kernel exists.
+TRAFFIC_PER_LAUNCH = {"k_dense_k5_tc": 16.20e9, "k_diag": 16.19e9}
 
 
 # ---------------------------------------------------------------------------
