@@ -403,6 +403,57 @@ def run_case(args):
     torch.cuda.synchronize()
 
 
+def run_batch_bench(args):
+    """Config 3: 512 QAOA circuits (widths 10..20) in one persistent launch
+    replayed as a CUDA graph, against one launch per block per circuit.
+    Prints its own JSON line (not the headline metric)."""
+    import torch
+    import paper_2410_09326_gb300 as qs
+    qs.load(build_if_missing=True)
+    circuits = cg.config3_batch(count=args.batch)
+    stream = torch.cuda.Stream()
+    states = [qs.qs_alloc_state(n, qs.QS_C64, stream=stream) for n, _ in circuits]
+    arrays = [qs.gates_to_array(g) for _, g in circuits]
+    t0 = time.perf_counter()
+    b = qs.qs_batch_create(states, arrays, qs.QS_DIAG, stream=stream)
+    create_s = time.perf_counter() - t0
+    info = qs.qs_batch_info(b)
+    for _ in range(args.warmup):
+        qs.qs_batch_run(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        qs.qs_batch_run(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # baseline: the same fused plans, one launch per block, circuit after circuit
+    flags = qs.QS_FUSE | qs.QS_FUSE_K(info.fuse_k) | qs.QS_DIAG
+    for _ in range(2):
+        e0.record(stream)
+        for (n, _), st, arr in zip(circuits, states, arrays):
+            qs.qs_set_basis(st, 0)
+            qs.qs_apply_circuit(st, arr, flags)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    base_ms = e0.elapsed_time(e1)
+    widths = sorted(set(n for n, _ in circuits))
+    line = {"config": "batch", "workload": f"{len(circuits)} QAOA Max-Cut circuits, widths {widths[0]}..{widths[-1]}, "
+                                           "p=1..4, complex64 from |0...0>",
+            "metric": "circuits/s", "value": round(len(circuits) / (ms * 1e-3), 1), "ms_per_batch": round(ms, 3),
+            "baseline_one_launch_per_block_ms": round(base_ms, 3),
+            "speedup_vs_per_circuit_launches": round(base_ms / ms, 2),
+            "gates": int(sum(a.size for a in arrays)), "fused_blocks": info.total_blocks,
+            "autotune": {"fuse_k": info.fuse_k, "threads": info.threads, "graph": bool(info.graph),
+                         "trials": [(info.tuned_k[i], info.tuned_threads[i], round(info.tuned_ms[i], 3))
+                                    for i in range(info.n_tuned)], "create_s": round(create_s, 2)}}
+    qs.qs_batch_free(b)
+    for st in states:
+        qs.qs_free_state(st)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,9 +466,15 @@ def main():
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
+    ap.add_argument("--config", default="main", choices=["main", "batch"],
+                    help="batch: the 512-circuit persistent-launch workload (own JSON line)")
+    ap.add_argument("--batch", type=int, default=512)
     args = ap.parse_args()
     if args.case:
         run_case(args)
+        return
+    if args.config == "batch":
+        run_batch_bench(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -305,6 +305,43 @@ qs_status qs_write_state(qs_state *st, const void *host_in);
 /* Device pointer of the amplitudes (for callers that share the buffer). */
 qs_status qs_device_ptr(const qs_state *st, void **out);
 
+/*
+ * Batches: many circuits of uneven width in one persistent launch, replayed
+ * as a CUDA graph (the paper's repeated runs of one circuit, Sec. IV-E, e.g.
+ * QAOA). qs_batch_create plans circuit c for states[c] (complex64, at most 26
+ * qubits, distinct buffers) and uploads every block once. Without QS_FUSE in
+ * flags the autotuner times fusion widths k = 2..4 x CTA sizes {256, 512,
+ * 1024} (opts->threads fixes the size) on the batch itself and keeps the
+ * fastest; QS_FUSE | QS_FUSE_K(k) fixes k (k >= 5 runs 256-thread CTAs).
+ * QS_VSWAP and QS_DIAG pass through to the planner. The chosen launch is captured as a CUDA
+ * graph on cuda_stream (NULL: a stream owned by the batch). Each
+ * qs_batch_run applies every circuit to its state starting from |0...0>
+ * (one CTA per circuit; states of <= 14 qubits stay in shared memory for the
+ * whole circuit), asynchronously, and sets each state's perm to its circuit's
+ * final logical->physical map. The states must outlive the batch.
+ */
+typedef struct qs_batch qs_batch;
+
+typedef struct {
+  int32_t count;          /* circuits */
+  int32_t fuse_k;         /* fusion width in use */
+  int32_t threads;        /* threads per CTA in use */
+  int32_t grid;           /* CTAs launched */
+  int32_t total_blocks;   /* fused blocks over all circuits */
+  int32_t graph;          /* 1 if runs replay a CUDA graph */
+  int32_t n_tuned;        /* autotuner trials recorded below */
+  int32_t tuned_k[16];
+  int32_t tuned_threads[16];
+  double tuned_ms[16];
+} qs_batch_info_t;
+
+qs_status qs_batch_create(qs_state *const *states, const qs_gate *const *gates, const size_t *n_gates, int count,
+                          uint64_t flags, const qs_opts *opts, void *cuda_stream, qs_batch **out);
+qs_status qs_batch_run(qs_batch *b);
+qs_status qs_batch_sync(qs_batch *b);   /* waits for the batch's stream */
+qs_status qs_batch_info(const qs_batch *b, qs_batch_info_t *out);
+void qs_batch_free(qs_batch *b);
+
 const char *qs_last_error(void);
 
 #ifdef __cplusplus

@@ -65,6 +65,13 @@ class qs_class_table(ctypes.Structure):
                 ("count", ctypes.c_int64 * QS_N_CLASSES)]
 
 
+class qs_batch_info_t(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("fuse_k", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("total_blocks", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("n_tuned", ctypes.c_int32), ("tuned_k", ctypes.c_int32 * 16),
+                ("tuned_threads", ctypes.c_int32 * 16), ("tuned_ms", ctypes.c_double * 16)]
+
+
 class qs_block_record(ctypes.Structure):
     _fields_ = [("index", ctypes.c_int32), ("kind", ctypes.c_uint8), ("k", ctypes.c_uint8),
                 ("nctrl", ctypes.c_uint8), ("tc", ctypes.c_uint8),
@@ -124,6 +131,13 @@ def load(build_if_missing=False):
         "qs_write_state": (ctypes.c_int, [vp, vp]),
         "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "qs_last_error": (ctypes.c_char_p, []),
+        "qs_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz),
+                                           ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(qs_opts), vp,
+                                           ctypes.POINTER(vp)]),
+        "qs_batch_run": (ctypes.c_int, [vp]),
+        "qs_batch_sync": (ctypes.c_int, [vp]),
+        "qs_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(qs_batch_info_t)]),
+        "qs_batch_free": (None, [vp]),
         "qs_probs_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.c_int, vp, vp]),
         "qs_plan": (ctypes.c_int, [ctypes.c_int, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts),
@@ -316,6 +330,39 @@ def qs_plan(n, gates, flags=QS_PLAIN, opts=None, perm=None):
         else:
             out.append(None)
     return list(recs)[: nb.value], out, np.array(list(pm), dtype=np.int64)
+
+
+def qs_batch_create(states, gate_arrays, flags=0, opts=None, stream=None):
+    """states: list of state handles; gate_arrays: list of GATE_DTYPE arrays."""
+    lib = load()
+    count = len(states)
+    arrs = [np.ascontiguousarray(g, dtype=GATE_DTYPE) for g in gate_arrays]
+    st = (ctypes.c_void_p * count)(*[s.value for s in states])
+    gp = (ctypes.c_void_p * count)(*[a.ctypes.data for a in arrs])
+    ng = (ctypes.c_size_t * count)(*[a.size for a in arrs])
+    h = ctypes.c_void_p()
+    _check(lib.qs_batch_create(st, gp, ng, count, flags, ctypes.byref(opts) if opts is not None else None,
+                               _stream_handle(stream), ctypes.byref(h)))
+    h._keep = arrs  # the library copies the gates; keep the arrays alive for the call only
+    return h
+
+
+def qs_batch_run(b):
+    _check(load().qs_batch_run(b))
+
+
+def qs_batch_sync(b):
+    _check(load().qs_batch_sync(b))
+
+
+def qs_batch_info(b):
+    info = qs_batch_info_t()
+    _check(load().qs_batch_info(b, ctypes.byref(info)))
+    return info
+
+
+def qs_batch_free(b):
+    load().qs_batch_free(b)
 
 
 def gates_to_array(gates):

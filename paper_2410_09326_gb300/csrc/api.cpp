@@ -56,6 +56,14 @@ struct qs_state {
   qs_class_table classes = {};
 };
 
+namespace qs {
+void *state_amps(qs_state *st) { return st->amps; }
+int state_n(const qs_state *st) { return st->n; }
+bool state_c64(const qs_state *st) { return st->dtype == QS_C64; }
+int8_t *state_perm(qs_state *st) { return st->perm; }
+cudaStream_t state_stream(const qs_state *st) { return st->stream; }
+}  // namespace qs
+
 namespace {
 
 int amp_bytes(const qs_state *st) { return st->dtype == QS_C128 ? 16 : 8; }
