@@ -306,6 +306,45 @@ qs_status qs_write_state(qs_state *st, const void *host_in);
 qs_status qs_device_ptr(const qs_state *st, void **out);
 
 /*
+ * Learned cost model. The paper leaves the mapping from profile data to
+ * optimisation flags open (Sec. III-A); here a 2 x 64 ReLU MLP predicts the
+ * natural log of a fused block's device time in ms from QS_MLP_FEATURES
+ * features of the block (qs_block_features), trained on block profiles the
+ * simulator records (QS_PROFILE). It replaces profiling runs: candidate plans
+ * are scored by their summed predicted block times.
+ *
+ * Parameters form one flat FP32 vector of QS_MLP_PARAMS values: W1 (64 x 24,
+ * row-major, out x in), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1);
+ * y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3. Training (qs_mlp_train)
+ * standardises inputs and targets with the training set's mean and standard
+ * deviation and runs Adam (beta1 0.9, beta2 0.999, eps 1e-8) on the mean
+ * squared error, with the library's own forward, backward and update kernels
+ * on the GPU. qs_mlp_gradient returns the gradient of the mean squared error
+ * on the inputs exactly as given (no standardisation), for checking.
+ */
+#define QS_MLP_FEATURES 24
+#define QS_MLP_HIDDEN 64
+#define QS_MLP_PARAMS (64 * 24 + 64 + 64 * 64 + 64 + 64 + 1)
+typedef struct qs_mlp qs_mlp;
+
+/* Features of profiled or planned blocks: count x QS_MLP_FEATURES floats. */
+qs_status qs_block_features(int n, qs_dtype dtype, const qs_block_record *recs, size_t count, float *out);
+qs_status qs_mlp_create(uint64_t seed, void *cuda_stream, qs_mlp **out);
+void qs_mlp_free(qs_mlp *m);
+/* Reads (host_out) and/or writes (host_in) the flat parameter vector. */
+qs_status qs_mlp_params(qs_mlp *m, float *host_out, const float *host_in);
+qs_status qs_mlp_gradient(qs_mlp *m, const float *x, const float *y, int n, float *grad_out, float *loss_out);
+/* Trains on n samples (host arrays); loss_out: last batch's loss in standardised units. */
+qs_status qs_mlp_train(qs_mlp *m, const float *x, const float *y, int n, int epochs, int batch, float lr,
+                       uint64_t seed, float *loss_out);
+/* Predicted log-milliseconds of n feature rows. */
+qs_status qs_mlp_predict(qs_mlp *m, const float *x, int n, float *y_out);
+/* Learned activator: the candidate flag set of qs_pgo_select with the least
+ * summed predicted block time; host planning + one batched prediction. */
+qs_status qs_pgo_select_mlp(qs_mlp *m, int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates,
+                            const qs_opts *opts, uint64_t *flags_out, double *predicted_ms);
+
+/*
  * Batches: many circuits of uneven width in one persistent launch, replayed
  * as a CUDA graph (the paper's repeated runs of one circuit, Sec. IV-E, e.g.
  * QAOA). qs_batch_create plans circuit c for states[c] (complex64, at most 26

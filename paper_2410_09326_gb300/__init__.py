@@ -36,6 +36,9 @@ def QS_FUSE_K(k):
 
 QS_N_GATE_TYPES = 33
 QS_N_CLASSES = 128
+QS_MLP_FEATURES = 24
+QS_MLP_HIDDEN = 64
+QS_MLP_PARAMS = 64 * 24 + 64 + 64 * 64 + 64 + 64 + 1
 QS_MAX_QUBITS = 40
 QS_MAX_DIAG = 10
 
@@ -131,6 +134,21 @@ def load(build_if_missing=False):
         "qs_write_state": (ctypes.c_int, [vp, vp]),
         "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "qs_last_error": (ctypes.c_char_p, []),
+        "qs_block_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qs_block_record), sz,
+                                             ctypes.POINTER(ctypes.c_float)]),
+        "qs_mlp_create": (ctypes.c_int, [ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
+        "qs_mlp_free": (None, [vp]),
+        "qs_mlp_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+        "qs_mlp_gradient": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                           ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float)]),
+        "qs_mlp_train": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_float)]),
+        "qs_mlp_predict": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_float)]),
+        "qs_pgo_select_mlp": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, sz, ctypes.POINTER(qs_opts),
+                                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
         "qs_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz),
                                            ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(qs_opts), vp,
                                            ctypes.POINTER(vp)]),
@@ -363,6 +381,73 @@ def qs_batch_info(b):
 
 def qs_batch_free(b):
     load().qs_batch_free(b)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def qs_block_features(n, recs, dtype=QS_C64):
+    """Feature rows (len(recs) x QS_MLP_FEATURES float32) of block records."""
+    arr = (qs_block_record * max(1, len(recs)))(*recs)
+    out = np.zeros((len(recs), QS_MLP_FEATURES), dtype=np.float32)
+    _check(load().qs_block_features(n, dtype, arr, len(recs), _fptr(out)))
+    return out
+
+
+def qs_mlp_create(seed=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().qs_mlp_create(seed, _stream_handle(stream), ctypes.byref(h)))
+    return h
+
+
+def qs_mlp_free(m):
+    load().qs_mlp_free(m)
+
+
+def qs_mlp_params(m, new=None):
+    """Returns the flat FP32 parameters; writes `new` first when given."""
+    out = np.zeros(QS_MLP_PARAMS, dtype=np.float32)
+    src = None
+    if new is not None:
+        src = np.ascontiguousarray(new, dtype=np.float32)
+        assert src.size == QS_MLP_PARAMS
+    _check(load().qs_mlp_params(m, _fptr(out), _fptr(src) if src is not None else None))
+    return out
+
+
+def qs_mlp_gradient(m, x, y):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    g = np.zeros(QS_MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float(0)
+    _check(load().qs_mlp_gradient(m, _fptr(x), _fptr(y), len(y), _fptr(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def qs_mlp_train(m, x, y, epochs=30, batch=256, lr=1e-3, seed=0):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    loss = ctypes.c_float(0)
+    _check(load().qs_mlp_train(m, _fptr(x), _fptr(y), len(y), epochs, batch, lr, seed, ctypes.byref(loss)))
+    return loss.value
+
+
+def qs_mlp_predict(m, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.zeros(len(x), dtype=np.float32)
+    _check(load().qs_mlp_predict(m, _fptr(x), len(x), _fptr(y)))
+    return y
+
+
+def qs_pgo_select_mlp(m, n, gates, dtype=QS_C64, opts=None):
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    f = ctypes.c_uint64(0)
+    ms = ctypes.c_double(0)
+    _check(load().qs_pgo_select_mlp(m, n, dtype, gates.ctypes.data_as(ctypes.c_void_p), gates.size,
+                                    ctypes.byref(opts) if opts is not None else None, ctypes.byref(f),
+                                    ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def gates_to_array(gates):

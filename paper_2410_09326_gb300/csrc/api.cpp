@@ -378,22 +378,9 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
       if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit");
     }
     qs_block_record r;
-    std::memset(&r, 0, sizeof(r));
-    r.index = (int32_t)i;
-    r.kind = (uint8_t)b.kind;
-    r.k = (uint8_t)b.k;
-    r.nctrl = (uint8_t)b.nctrl;
-    r.tc = b.tc ? 1 : 0;
-    for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
-    r.meta = (uint8_t)b.meta;
-    r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
-    r.n_gates = b.n_gates;
-      r.cmask = b.cmask;
-    r.bytes = block_bytes(b, st->n, ab);
+    fill_record(b, (int)i, st->n, ab, r);
     st->rec_class.push_back(block_class(b));
     st->h2d_bytes += (double)block_param_bytes(b, c128);
-    r.t_start_ms = -1;
-    r.ms = -1;
     st->recs.push_back(r);
   }
   std::memcpy(st->perm, perm, sizeof(perm));
@@ -456,6 +443,25 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
   return QS_OK;
 }
 
+qs_status qs_block_features(int n, qs_dtype dtype, const qs_block_record *recs, size_t count, float *out) {
+  if ((count && (!recs || !out)) || n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qs_block_features: bad arguments");
+  for (size_t i = 0; i < count; i++) record_features(recs[i], n, dtype == QS_C128, out + i * QS_MLP_FEATURES);
+  return QS_OK;
+}
+
+qs_status qs_pgo_select_mlp(qs_mlp *m, int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates,
+                            const qs_opts *opts, uint64_t *flags_out, double *predicted_ms) {
+  if (!m || !flags_out || (n_gates && !gates)) return fail(QS_EINVAL, "qs_pgo_select_mlp: null argument");
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qs_pgo_select_mlp: qubit count out of range");
+  qs_opts o;
+  if (opts) o = *opts;
+  else qs_default_opts(&o);
+  std::string err;
+  qs_status s = mlp_select(m, n, dtype == QS_C128, gates, n_gates, o, flags_out, predicted_ms, err);
+  if (s != QS_OK) return fail(s, "qs_pgo_select_mlp: " + err);
+  return QS_OK;
+}
+
 qs_status qs_profile_reset(qs_state *st) {
   if (!st) return fail(QS_EINVAL, "null state");
   std::memset(&st->classes, 0, sizeof(st->classes));
@@ -487,24 +493,7 @@ qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, c
   size_t mlen = 0;
   for (size_t i = 0; i < plan.size(); i++) {
     const Block &b = plan[i];
-    if (recs && i < cap) {
-      qs_block_record r;
-      std::memset(&r, 0, sizeof(r));
-      r.index = (int32_t)i;
-      r.kind = (uint8_t)b.kind;
-      r.k = (uint8_t)b.k;
-      r.nctrl = (uint8_t)b.nctrl;
-      r.tc = b.tc ? 1 : 0;
-      for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
-      r.meta = (uint8_t)b.meta;
-      r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
-      r.n_gates = b.n_gates;
-      r.cmask = b.cmask;
-      r.bytes = block_bytes(b, n, 8);
-      r.t_start_ms = -1;
-      r.ms = -1;
-      recs[i] = r;
-    }
+    if (recs && i < cap) fill_record(b, (int)i, n, 8, recs[i]);
     for (const cd &z : b.mat) {
       if (mats && mlen < mats_cap) {
         mats[2 * mlen] = z.real();

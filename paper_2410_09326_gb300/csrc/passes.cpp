@@ -222,6 +222,23 @@ bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_p
 
 void parallel_blocks(size_t n, const std::function<void(size_t)> &f) { parallel_for(n, f); }
 
+void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_record &r) {
+  std::memset(&r, 0, sizeof(r));
+  r.index = (int32_t)index;
+  r.kind = (uint8_t)b.kind;
+  r.k = (uint8_t)b.k;
+  r.nctrl = (uint8_t)b.nctrl;
+  r.tc = b.tc ? 1 : 0;
+  for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
+  r.meta = (uint8_t)b.meta;
+  r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
+  r.n_gates = b.n_gates;
+  r.cmask = b.cmask;
+  r.bytes = block_bytes(b, n, amp_bytes);
+  r.t_start_ms = -1;
+  r.ms = -1;
+}
+
 double block_bytes(const Block &b, int n, int amp_bytes) {
   double amps = std::ldexp(1.0, n - b.nctrl);
   if (b.kind == BK_PERMUTE) amps = std::ldexp(1.0, n - 1);

@@ -106,11 +106,50 @@ uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts
 }
 
 
-qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
-                          const qs_class_table *t, uint64_t base, uint64_t *flags_out, double *pred_ms,
-                          std::string &err) {
-  const uint64_t keep = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_TC | (15ull << 16) |
-                                           QS_PGO_RULES | QS_PGO_MEASURED);
+void record_features(const qs_block_record &r, int n, bool c128, float *f) {
+  for (int i = 0; i < QS_MLP_FEATURES; i++) f[i] = 0.f;
+  int k = r.kind == BK_PERMUTE ? 2 : r.k;
+  int tmin = 64, tmax = -1, low5 = 0, high = 0;
+  bool bit[64] = {false};
+  for (int j = 0; j < k && j < QS_MAX_DIAG; j++) {
+    const int q = r.qubits[j];
+    if (q < 0) continue;
+    bit[q] = true;
+    tmin = std::min(tmin, q);
+    tmax = std::max(tmax, q);
+    if (q < 5) low5++;
+    if (q >= n - 6) high++;
+  }
+  f[0] = n / 32.f;
+  f[1] = k / 6.f;
+  f[2] = r.nctrl / 8.f;
+  f[3] = r.kind == BK_DENSE;
+  f[4] = r.kind == BK_DIAG;
+  f[5] = r.kind == BK_PERMUTE;
+  f[6] = r.tc ? 1.f : 0.f;
+  f[7] = (r.kind == BK_DENSE && bit[0] && bit[1]) ? 1.f : 0.f;
+  f[8] = tmax >= 0 ? tmin / (float)n : 0.f;
+  f[9] = tmax >= 0 ? tmax / (float)n : 0.f;
+  f[10] = low5 / 6.f;
+  f[11] = high / 6.f;
+  f[12] = std::log2((float)r.n_gates + 1.f) / 8.f;
+  f[13] = (float)(std::log2(r.bytes > 1 ? r.bytes : 1.0) / 40.0);
+  for (int j = 0; j < 5; j++) f[14 + j] = bit[j] ? 1.f : 0.f;
+  for (int q = 5; q < 64; q++)
+    if (bit[q]) {
+      if (q < 10) f[19] = 1.f;
+      else if (q < 20) f[20] = 1.f;
+      else f[21] = 1.f;
+    }
+  f[22] = c128 ? 1.f : 0.f;
+  f[23] = r.meta == 4 ? 1.f : 0.f;
+}
+
+namespace {
+
+// The flag sets both activators choose among: plain, virtual swap alone,
+// and fusion k = 1..6 with diagonal runs (tensor cores for k >= 4, c64).
+std::vector<uint64_t> candidate_flags(const qs_gate *gates, size_t n_gates, bool c128) {
   bool has_swap = false;
   for (size_t i = 0; i < n_gates; i++) has_swap |= gates[i].op == QS_SWAP;
   std::vector<uint64_t> cands;
@@ -121,6 +160,62 @@ qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates
     cands.push_back(vs | QS_FUSE | QS_FUSE_K(k) | QS_DIAG);
     if (k >= 4 && !c128) cands.push_back(vs | QS_FUSE | QS_FUSE_K(k) | QS_DIAG | QS_TC);
   }
+  return cands;
+}
+
+}  // namespace
+
+qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
+                     uint64_t *flags_out, double *pred_ms, std::string &err) {
+  const std::vector<uint64_t> cands = candidate_flags(gates, n_gates, c128);
+  std::vector<float> feats;
+  std::vector<size_t> first(cands.size() + 1, 0);
+  std::vector<Block> plan;
+  PlanStats stats;
+  for (size_t c = 0; c < cands.size(); c++) {
+    int8_t perm[QS_MAX_QUBITS];
+    for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
+    qs_status s = build_plan(n, gates, n_gates, cands[c], o, perm, plan, stats, err);
+    if (s != QS_OK) return s;
+    first[c] = feats.size() / QS_MLP_FEATURES;
+    for (size_t i = 0; i < plan.size(); i++) {
+      qs_block_record r;
+      fill_record(plan[i], (int)i, n, c128 ? 16 : 8, r);
+      feats.resize(feats.size() + QS_MLP_FEATURES);
+      record_features(r, n, c128, feats.data() + feats.size() - QS_MLP_FEATURES);
+    }
+  }
+  first[cands.size()] = feats.size() / QS_MLP_FEATURES;
+  const int total = (int)first[cands.size()];
+  std::vector<float> y(total > 0 ? total : 1);
+  if (total > 0) {
+    qs_status s = qs_mlp_predict(mm, feats.data(), total, y.data());
+    if (s != QS_OK) {
+      err = "cost-model prediction failed";
+      return s;
+    }
+  }
+  double best = 1e300;
+  uint64_t best_f = cands[0];
+  for (size_t c = 0; c < cands.size(); c++) {
+    double ms = 0;
+    for (size_t i = first[c]; i < first[c + 1]; i++) ms += std::exp((double)y[i]) + 0.004;
+    if (ms < best * 0.999) {
+      best = ms;
+      best_f = cands[c];
+    }
+  }
+  *flags_out = best_f;
+  if (pred_ms) *pred_ms = best;
+  return QS_OK;
+}
+
+qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
+                          const qs_class_table *t, uint64_t base, uint64_t *flags_out, double *pred_ms,
+                          std::string &err) {
+  const uint64_t keep = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_TC | (15ull << 16) |
+                                           QS_PGO_RULES | QS_PGO_MEASURED);
+  const std::vector<uint64_t> cands = candidate_flags(gates, n_gates, c128);
   const double peak = o.peak_gbs > 0 ? o.peak_gbs : 6688.8;
   double best = 1e300;
   uint64_t best_f = cands[0];

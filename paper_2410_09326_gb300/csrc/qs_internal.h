@@ -73,6 +73,12 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
 
 double block_bytes(const Block &b, int n, int amp_bytes);
 
+// The public record of a planned block (passes.cpp).
+void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_record &r);
+
+// Cost-model features of a block record (pgo.cpp).
+void record_features(const qs_block_record &r, int n, bool c128, float *f);
+
 // f(0..n) on a few host threads (passes.cpp).
 void parallel_blocks(size_t n, const std::function<void(size_t)> &f);
 
@@ -84,6 +90,8 @@ double predict_plan_ms(const std::vector<Block> &plan, int n, int amp_bytes, con
 qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
                           const qs_class_table *t, uint64_t base, uint64_t *flags_out, double *pred_ms,
                           std::string &err);
+qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
+                     uint64_t *flags_out, double *pred_ms, std::string &err);
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels.cu). All asynchronous on `s`.

@@ -324,3 +324,36 @@ def test_parser_rejects_bad_input():
                 "qreg q[2];\nfoo q[0];\n", "h q[0];\n", "qreg q[2];\nh q[0]\n"]:
         with pytest.raises(ValueError):
             oracle.simulate(bad)
+
+
+# ---------------------------------------------------------------------------
+# Cost-model network reference (oracle/mlp.py)
+# ---------------------------------------------------------------------------
+
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    p = rng.normal(scale=0.3, size=mlp.N_PARAMS)
+    x = rng.normal(size=(7, mlp.F))
+    t = rng.normal(size=7)
+    g = mlp.gradient(p, x, t)
+    h = 1e-6
+    for i in list(range(0, mlp.N_PARAMS, 97)) + [mlp.N_PARAMS - 1, mlp.N_PARAMS - 2]:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mlp.loss(p + e, x, t) - mlp.loss(p - e, x, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), i
+
+
+def test_mlp_linear_regime_closed_form():
+    """With every pre-activation positive the network is one affine map."""
+    from oracle import mlp
+    rng = np.random.default_rng(4)
+    w = {"W1": rng.uniform(0.1, 1, (mlp.H, mlp.F)), "b1": rng.uniform(0.1, 1, mlp.H),
+         "W2": rng.uniform(0.1, 1, (mlp.H, mlp.H)), "b2": rng.uniform(0.1, 1, mlp.H),
+         "w3": rng.normal(size=mlp.H), "b3": np.array([0.5])}
+    x = rng.uniform(0, 1, (5, mlp.F))
+    y, _ = mlp.forward(mlp.pack(w), x)
+    want = ((x @ w["W1"].T + w["b1"]) @ w["W2"].T + w["b2"]) @ w["w3"] + 0.5
+    assert np.allclose(y, want, rtol=1e-13)
+    assert mlp.N_PARAMS == 64 * 24 + 64 + 64 * 64 + 64 + 64 + 1
