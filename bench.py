@@ -28,6 +28,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 import circuitgen as cg  # noqa: E402
+import numpy as np  # noqa: E402
 
 N_QUBITS = 30
 MEASURED_QUBITS = 16
@@ -454,6 +455,61 @@ def run_batch_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_costmodel_bench(args):
+    """Config 4: train the MLP cost model on profiled blocks of seeded
+    circuits (n = 20..28), then choose flags for unseen n = 30 GHZ / QFT /
+    random circuits; regret of each activator against brute force over the
+    candidate flag sets (all measured on this GPU). Own JSON line."""
+    import torch
+    import paper_2410_09326_gb300 as qs
+    from paper_2410_09326_gb300 import costmodel
+    qs.load(build_if_missing=True)
+    t0 = time.perf_counter()
+    train = costmodel.training_circuits(args.train_circuits, n_lo=20, n_hi=28, index0=1000)
+    x, y = costmodel.build_dataset(train)
+    t_data = time.perf_counter() - t0
+    m = qs.qs_mlp_create(7)
+    t0 = time.perf_counter()
+    loss = qs.qs_mlp_train(m, x, y, epochs=40, batch=256, lr=2e-3, seed=3)
+    t_train = time.perf_counter() - t0
+    n = N_QUBITS
+    c = cg.config1_circuits(n=n, index=9)
+    unseen = {"ghz": c["ghz"][1], "qft": c["qft"][1], "random": c["random"][1]}
+    flat = qs.qs_class_table()
+    for k in range(qs.QS_N_CLASSES):
+        flat.bytes[k], flat.ms[k], flat.count[k] = 6e9, 1.0, 1
+    cands = [qs.QS_PLAIN, qs.QS_VSWAP] + [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)] + \
+            [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | qs.QS_TC for k in (4, 5, 6)]
+    out = {}
+    for name, gates in unseen.items():
+        arr = qs.gates_to_array(gates)
+        meas = costmodel.measure_candidates(n, gates, cands, repeats=1)
+        best_f = min(meas, key=meas.get)
+        choices = {}
+        t1 = time.perf_counter()
+        choices["mlp"] = qs.qs_pgo_select_mlp(m, n, arr)[0]
+        t_sel = (time.perf_counter() - t1) * 1e3
+        choices["priors"] = qs.qs_pgo_select(n, arr)[0]
+        choices["bytes_only"] = qs.qs_pgo_select(n, arr, table=flat)[0]
+        res = {"best_ms": round(meas[best_f], 2), "best_flags": hex(best_f), "mlp_select_ms": round(t_sel, 1)}
+        for who, f in choices.items():
+            t = meas.get(f)
+            if t is None:
+                t = costmodel.measure_candidates(n, gates, [f], repeats=1)[f]
+            res[who] = {"flags": hex(f), "regret": round(t / meas[best_f], 3)}
+        fx, fy, _ = costmodel.profile_blocks(n, gates, choices["mlp"])
+        res["mlp_block_log_err"] = round(float(np.mean(np.abs(qs.qs_mlp_predict(m, fx) - fy))), 3)
+        out[name] = res
+    qs.qs_mlp_free(m)
+    torch.cuda.synchronize()
+    line = {"config": "costmodel", "workload": f"train: {len(train)} seeded circuits n=20..28 (random layered, "
+                                                f"QFT, GHZ, QAOA) x {len(costmodel.TRAIN_FLAGS)} flag sets; test: "
+                                                "unseen n=30 GHZ / QFT / random",
+            "samples": int(len(y)), "profiling_s": round(t_data, 1), "train_s": round(t_train, 2),
+            "final_loss_std_units": round(loss, 4), "candidates": len(cands), "unseen": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,8 +522,9 @@ def main():
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
-    ap.add_argument("--config", default="main", choices=["main", "batch"],
-                    help="batch: the 512-circuit persistent-launch workload (own JSON line)")
+    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel"],
+                    help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
+    ap.add_argument("--train-circuits", type=int, default=60)
     ap.add_argument("--batch", type=int, default=512)
     args = ap.parse_args()
     if args.case:
@@ -475,6 +532,9 @@ def main():
         return
     if args.config == "batch":
         run_batch_bench(args)
+        return
+    if args.config == "costmodel":
+        run_costmodel_bench(args)
         return
     if args.warmup < 3:
         args.warmup = 3
