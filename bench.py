@@ -510,6 +510,47 @@ def run_costmodel_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_tc32_bench(args):
+    """Config 2: n=32 complex64 (32 GiB), 40 layers of U3 + CX/CZ; fused k=4..6
+    blocks on tensor cores against the FP32 CUDA-core kernels; the tensor-core
+    result is compared with an FP64 (complex128, 64 GiB) GPU run of the same
+    circuit. Own JSON line."""
+    import torch
+    import paper_2410_09326_gb300 as qs
+    qs.load(build_if_missing=True)
+    n = args.n if args.n != 26 else 32
+    _, gates = cg.config2_circuit(n=n, layers=40)
+    arr = qs.gates_to_array(gates)
+    V = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_DIAG
+    variants = {"tc_k4": V | qs.QS_FUSE_K(4) | qs.QS_TC, "tc_k5": V | qs.QS_FUSE_K(5) | qs.QS_TC,
+                "cuda_k3": V | qs.QS_FUSE_K(3), "cuda_k4": V | qs.QS_FUSE_K(4), "cuda_k5": V | qs.QS_FUSE_K(5)}
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    res = {}
+    for name, f in variants.items():
+        qs.qs_set_basis(st, 0)
+        qs.qs_apply_circuit(st, arr, f | qs.QS_PROFILE)
+        summ, recs = qs.qs_profile(st)
+        res[name] = {"ms": round(summ.total_ms, 1), "blocks": summ.n_blocks,
+                     "gbs": round(summ.total_bytes / summ.total_ms / 1e6, 1)}
+    best = min(res, key=lambda k: res[k]["ms"])
+    # leave the state at the fastest tensor-core variant's result
+    qs.qs_set_basis(st, 0)
+    qs.qs_apply_circuit(st, arr, variants["tc_k5"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ref = qs.qs_alloc_state(n, qs.QS_C128)
+    qs.qs_apply_circuit(ref, arr, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(3) | qs.QS_DIAG)
+    dist = qs.qs_state_distance(st, ref)
+    fp64_s = time.perf_counter() - t0
+    norm = qs.qs_norm(st)
+    qs.qs_free_state(ref)
+    qs.qs_free_state(st)
+    line = {"config": "tc32", "workload": f"n={n} complex64, 40 layers of U3 (angles U[0,2pi)) + CX/CZ on a random "
+                                          f"matching ({len(gates)} gates)", "variants": res, "fastest": best,
+            "l2_error_tc_k5_vs_fp64_gpu": dist, "norm_tc_k5": norm, "fp64_run_s": round(fp64_s, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,7 +563,7 @@ def main():
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
-    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel"],
+    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32"],
                     help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
     ap.add_argument("--train-circuits", type=int, default=60)
     ap.add_argument("--batch", type=int, default=512)
@@ -535,6 +576,9 @@ def main():
         return
     if args.config == "costmodel":
         run_costmodel_bench(args)
+        return
+    if args.config == "tc32":
+        run_tc32_bench(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -299,6 +299,15 @@ qs_status qs_norm(qs_state *st, double *host_out);
  */
 qs_status qs_read_state(qs_state *st, void *host_out, int logical_order);
 
+/*
+ * L2 distance sqrt(sum_i |a_i - b_i|^2) between two states of the same width
+ * (any dtypes, FP64 accumulation on the GPU) in logical order: when their
+ * maps differ both are first brought to perm = identity on the GPU. For
+ * validating a complex64 run against a complex128 one without copying the
+ * states to the host. Synchronises both streams.
+ */
+qs_status qs_state_distance(qs_state *a, qs_state *b, double *out);
+
 /* Copies 2^n amplitudes from host memory into the state (physical layout). */
 qs_status qs_write_state(qs_state *st, const void *host_in);
 

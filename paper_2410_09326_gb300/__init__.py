@@ -132,6 +132,7 @@ def load(build_if_missing=False):
         "qs_norm": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double)]),
         "qs_read_state": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "qs_write_state": (ctypes.c_int, [vp, vp]),
+        "qs_state_distance": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
         "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "qs_last_error": (ctypes.c_char_p, []),
         "qs_block_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qs_block_record), sz,
@@ -303,6 +304,12 @@ def qs_read_state(st, n, dtype=QS_C64, logical_order=False, out=None):
         out = np.empty(1 << n, dtype=npdt)
     _check(load().qs_read_state(st, out.ctypes.data_as(ctypes.c_void_p), 1 if logical_order else 0))
     return out
+
+
+def qs_state_distance(a, b):
+    out = ctypes.c_double(0)
+    _check(load().qs_state_distance(a, b, ctypes.byref(out)))
+    return out.value
 
 
 def qs_write_state(st, host):

@@ -122,6 +122,22 @@ qs_status resolve_records(qs_state *st, bool wait) {
 
 qs_status fold_records(qs_state *st, bool wait) { return resolve_records(st, wait); }
 
+// Undoes the relabelling with physical bit exchanges (one per cycle step),
+// leaving perm = identity.
+cudaError_t to_logical_order(qs_state *st) {
+  for (int l = 0; l < st->n; l++) {
+    if (st->perm[l] == l) continue;
+    int other = -1;
+    for (int k = 0; k < st->n; k++)
+      if (st->perm[k] == l) other = k;
+    cudaError_t e = launch_permute(st->amps, st->n, st->dtype == QS_C128, st->perm[l], l, st->stream);
+    if (e != cudaSuccess) return e;
+    st->perm[other] = st->perm[l];
+    st->perm[l] = (int8_t)l;
+  }
+  return cudaSuccess;
+}
+
 qs_status check_state(const qs_state *st) {
   if (!st) return fail(QS_EINVAL, "null state");
   if (st->bad) return fail(QS_ESTATE, "state invalid after an earlier CUDA error");
@@ -541,22 +557,46 @@ qs_status qs_read_state(qs_state *st, void *host_out, int logical_order) {
   DeviceGuard dg(st->device);
   cudaError_t e = cudaSuccess;
   if (logical_order) {
-    // undo the relabelling with physical bit exchanges, one per cycle step
-    for (int l = 0; l < st->n; l++) {
-      if (st->perm[l] == l) continue;
-      int other = -1;
-      for (int k = 0; k < st->n; k++)
-        if (st->perm[k] == l) other = k;
-      e = launch_permute(st->amps, st->n, st->dtype == QS_C128, st->perm[l], l, st->stream);
-      if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
-      st->perm[other] = st->perm[l];
-      st->perm[l] = (int8_t)l;
-    }
+    e = to_logical_order(st);
+    if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
   }
   e = cudaMemcpyAsync(host_out, st->amps, (size_t)amp_bytes(st) << st->n, cudaMemcpyDeviceToHost, st->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);
   if (e != cudaSuccess) return cuda_fail(st, e, "qs_read_state");
   return check_device_error(st);
+}
+
+qs_status qs_state_distance(qs_state *a, qs_state *b, double *out) {
+  qs_status s = check_state(a);
+  if (s == QS_OK) s = check_state(b);
+  if (s != QS_OK) return s;
+  if (!out || a == b) return fail(QS_EINVAL, "qs_state_distance: bad arguments");
+  if (a->n != b->n || a->device != b->device) return fail(QS_EINVAL, "qs_state_distance: states differ in size or device");
+  DeviceGuard dg(a->device);
+  cudaError_t e = cudaSuccess;
+  if (std::memcmp(a->perm, b->perm, a->n) != 0) {
+    e = to_logical_order(a);
+    if (e == cudaSuccess) e = to_logical_order(b);
+    if (e != cudaSuccess) return cuda_fail(a, e, "qs_state_distance");
+  }
+  // b's stream waits for a's work; the reduction runs on b's stream
+  if (a->stream != b->stream) {
+    e = cudaStreamSynchronize(a->stream);
+    if (e != cudaSuccess) return cuda_fail(a, e, "qs_state_distance");
+  }
+  const int grid = distance_grid();
+  e = grow(b->d_partial, b->partial_cap, (size_t)grid);
+  if (e != cudaSuccess) return fail(QS_ENOMEM, "scratch allocation failed");
+  e = launch_distance(a->amps, a->dtype == QS_C128, b->amps, b->dtype == QS_C128, a->n, b->d_partial, b->stream);
+  std::vector<double> part(grid);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), b->d_partial, sizeof(double) * grid, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "qs_state_distance");
+  double sum = 0;
+  for (double v : part) sum += v;
+  *out = std::sqrt(sum);
+  return QS_OK;
 }
 
 qs_status qs_write_state(qs_state *st, const void *host_in) {

@@ -521,6 +521,26 @@ __global__ void __launch_bounds__(256) k_probs_chunk(const T *__restrict__ a, co
   if (__syncthreads_or(dirty)) flush(cur_hi);
 }
 
+// sum |a_i - b_i|^2 over i, one FP64 partial per CTA (fixed-order reduce)
+template <typename Ta, typename Tb>
+__global__ void __launch_bounds__(256) k_distance(const Ta *__restrict__ a, const Tb *__restrict__ b, long long N,
+                                                  double *__restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+    const double dx = (double)a[i].x - (double)b[i].x, dy = (double)a[i].y - (double)b[i].y;
+    s += dx * dx + dy * dy;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
 template <typename T> size_t param_bytes_t(const Block &b) {
   if (b.kind == BK_PERMUTE) return sizeof(T *) + sizeof(long long) + 2 * sizeof(int);
   if (b.kind == BK_DIAG) return sizeof(T *) + sizeof(DiagParam<T>);
@@ -554,6 +574,19 @@ cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStr
   if (e != cudaSuccess) return e;
   if (c128) k_set_one<double2><<<1, 1, 0, s>>>((double2 *)amps, idx);
   else k_set_one<float2><<<1, 1, 0, s>>>((float2 *)amps, idx);
+  return cudaGetLastError();
+}
+
+int distance_grid() { return dev_info().sms * 4; }
+
+cudaError_t launch_distance(const void *a, bool a128, const void *b, bool b128, int n, double *partial,
+                            cudaStream_t s) {
+  const long long N = 1ll << n;
+  const int grid = distance_grid();
+  if (!a128 && !b128) k_distance<float2, float2><<<grid, 256, 0, s>>>((const float2 *)a, (const float2 *)b, N, partial);
+  else if (!a128 && b128) k_distance<float2, double2><<<grid, 256, 0, s>>>((const float2 *)a, (const double2 *)b, N, partial);
+  else if (a128 && !b128) k_distance<double2, float2><<<grid, 256, 0, s>>>((const double2 *)a, (const float2 *)b, N, partial);
+  else k_distance<double2, double2><<<grid, 256, 0, s>>>((const double2 *)a, (const double2 *)b, N, partial);
   return cudaGetLastError();
 }
 

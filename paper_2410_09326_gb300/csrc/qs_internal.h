@@ -122,6 +122,10 @@ cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStr
 // partial: device scratch of probs_scratch_doubles(n, m) doubles; out: 2^m
 // doubles on the device.
 size_t probs_scratch_doubles(int n, int m);
+// sum |a_i - b_i|^2 into distance_grid() FP64 partials
+int distance_grid();
+cudaError_t launch_distance(const void *a, bool a128, const void *b, bool b128, int n, double *partial,
+                            cudaStream_t s);
 cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int m,
                          double *partial, double *out, cudaStream_t s);
 
