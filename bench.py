@@ -125,13 +125,22 @@ def dist_env():
 
 
 def max_over_ranks(x, world):
+    """Maximum of a per-rank number over all ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(bytes_per_step_per_rank, ms_per_step_max, world):
+    """Whole-job throughput (GB/s): every rank processes its own replica of the
+    workload, so the job moves world x the per-rank bytes in the slowest
+    rank's time."""
+    return bytes_per_step_per_rank * world / (ms_per_step_max * 1e-3) / 1e9
 
 
 def barrier(world):
@@ -216,7 +225,7 @@ def run_ours(args):
     wall_max = max_over_ranks(wall, world)
     ms_per_step = ms_max / args.steps
     bytes_per_step = tot_bytes / args.steps
-    value = bytes_per_step * world / (ms_per_step * 1e-3) / 1e9
+    value = aggregate_value(bytes_per_step, ms_per_step, world)
     # end to end: host wall clock around the same public calls, which parse
     # the text, ship gate data as launch parameters and read the marginal
     # probabilities back (2^16 doubles per circuit)
