@@ -90,6 +90,7 @@ typedef struct {
 #define QS_TC ((uint64_t)1 << 3)            /* dense k>=4 blocks on tensor cores */
 #define QS_PROFILE ((uint64_t)1 << 4)       /* time every block with CUDA events */
 #define QS_RELOCATE ((uint64_t)1 << 5)      /* profile-guided hot-qubit relocation */
+#define QS_FOLD ((uint64_t)1 << 6)          /* rotation folding + pair cancellation first */
 #define QS_PGO_RULES ((uint64_t)1 << 8)     /* pick flags with the paper's counter rules */
 #define QS_PGO_MEASURED ((uint64_t)1 << 9)  /* pick flags from a measured block profile */
 #define QS_FUSE_K(k) ((uint64_t)((k) & 15) << 16)
@@ -251,6 +252,17 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
 qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, const qs_opts *opts,
                   int8_t *perm_inout, qs_block_record *recs, size_t cap, size_t *n_blocks,
                   double *mats, size_t mats_cap, size_t *mats_len);
+
+/*
+ * Rotation folding (Sec. III-D): phase rotations (T, T^dagger, S, S^dagger,
+ * Z, U1, RZ) on the same parity of a CNOT/X/SWAP/diagonal region merge into
+ * the first of them (e.g. T . T -> S), then adjacent equal self-inverse gates
+ * cancel (CNOT . CNOT, H . H, ...). The result is the same unitary, global
+ * phase included (a nonzero phase is appended as U1, RZ on qubit 0). Host
+ * only. Writes up to cap gates; *n_out receives the count (QS_EINVAL when it
+ * exceeds cap).
+ */
+qs_status qs_fold_rotations(int n, const qs_gate *in, size_t n_in, qs_gate *out, size_t cap, size_t *n_out);
 
 /* Logical->physical map: perm_out[l] = physical bit of logical qubit l (n entries). */
 qs_status qs_get_perm(const qs_state *st, int8_t *perm_out);

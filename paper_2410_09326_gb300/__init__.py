@@ -26,6 +26,7 @@ QS_DIAG = 1 << 2
 QS_TC = 1 << 3
 QS_PROFILE = 1 << 4
 QS_RELOCATE = 1 << 5
+QS_FOLD = 1 << 6
 QS_PGO_RULES = 1 << 8
 QS_PGO_MEASURED = 1 << 9
 
@@ -133,6 +134,7 @@ def load(build_if_missing=False):
         "qs_read_state": (ctypes.c_int, [vp, vp, ctypes.c_int]),
         "qs_write_state": (ctypes.c_int, [vp, vp]),
         "qs_state_distance": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
+        "qs_fold_rotations": (ctypes.c_int, [ctypes.c_int, vp, sz, vp, sz, ctypes.POINTER(sz)]),
         "qs_device_ptr": (ctypes.c_int, [vp, ctypes.POINTER(vp)]),
         "qs_last_error": (ctypes.c_char_p, []),
         "qs_block_features": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(qs_block_record), sz,
@@ -303,6 +305,29 @@ def qs_read_state(st, n, dtype=QS_C64, logical_order=False, out=None):
     if out is None:
         out = np.empty(1 << n, dtype=npdt)
     _check(load().qs_read_state(st, out.ctypes.data_as(ctypes.c_void_p), 1 if logical_order else 0))
+    return out
+
+
+def qs_fold_rotations(n, gates):
+    """Rotation folding + pair cancellation (host only): returns the new gate array."""
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    cap = gates.size + 2
+    out = np.zeros(cap, dtype=GATE_DTYPE)
+    cnt = ctypes.c_size_t(0)
+    _check(load().qs_fold_rotations(n, gates.ctypes.data_as(ctypes.c_void_p), gates.size,
+                                    out.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(cnt)))
+    return out[: cnt.value].copy()
+
+
+def array_to_gates(arr):
+    """GATE_DTYPE array -> (name, qubits, params) tuples (for printing as text)."""
+    out = []
+    for a in arr:
+        name = OPS[a["op"]]
+        nq = int(a["nq"])
+        npar = {"rx": 1, "ry": 1, "rz": 1, "cp": 1, "cu1": 1, "crx": 1, "cry": 1, "crz": 1, "u1": 1,
+                "rzz": 1, "rxx": 1, "ryy": 1, "u2": 2, "u3": 3, "cu3": 3}.get(name, 0)
+        out.append((name, [int(x) for x in a["q"][:nq]], [float(x) for x in a["p"][:npar]]))
     return out
 
 

@@ -459,6 +459,25 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
   return QS_OK;
 }
 
+qs_status qs_fold_rotations(int n, const qs_gate *in, size_t n_in, qs_gate *out, size_t cap, size_t *n_out) {
+  if (n < 1 || n > QS_MAX_QUBITS || (n_in && !in) || !n_out) return fail(QS_EINVAL, "qs_fold_rotations: bad arguments");
+  std::vector<Block> plan;
+  PlanStats stats;
+  std::string err;
+  int8_t perm[QS_MAX_QUBITS];
+  for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
+  qs_opts o;
+  qs_default_opts(&o);
+  // validation of the input gates
+  qs_status s = build_plan(n, in, n_in, QS_PLAIN, o, perm, plan, stats, err);
+  if (s != QS_OK) return fail(s, "qs_fold_rotations: " + err);
+  std::vector<qs_gate> f = fold_rotations(n, in, n_in);
+  *n_out = f.size();
+  if (f.size() > cap) return fail(QS_EINVAL, "qs_fold_rotations: output buffer too small");
+  if (!f.empty()) std::memcpy(out, f.data(), f.size() * sizeof(qs_gate));
+  return QS_OK;
+}
+
 qs_status qs_block_features(int n, qs_dtype dtype, const qs_block_record *recs, size_t count, float *out) {
   if ((count && (!recs || !out)) || n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qs_block_features: bad arguments");
   for (size_t i = 0; i < count; i++) record_features(recs[i], n, dtype == QS_C128, out + i * QS_MLP_FEATURES);

@@ -290,6 +290,15 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
 
+  // (0) rotation folding (an IR rewrite; exact)
+  std::vector<qs_gate> folded;
+  if (flags & QS_FOLD) {
+    folded = fold_rotations(n, gates, n_gates);
+    stats.gates_removed = (int)n_gates - (int)folded.size();
+    gates = folded.data();
+    n_gates = folded.size();
+  }
+
   // (1) virtual swap and renaming to physical qubits
   std::vector<qs_gate> pg;
   pg.reserve(n_gates);

@@ -62,6 +62,7 @@ struct PlanStats {
   int gates_in = 0;
   int swaps_absorbed = 0;
   int relocations = 0;
+  int gates_removed = 0;  // by rotation folding
 };
 
 // Virtual swap + fusion + classification. Gates are logical; perm is the
@@ -81,6 +82,10 @@ void record_features(const qs_block_record &r, int n, bool c128, float *f);
 
 // f(0..n) on a few host threads (passes.cpp).
 void parallel_blocks(size_t n, const std::function<void(size_t)> &f);
+
+// Rotation folding + peephole cancellation (fold.cpp): an equivalent gate
+// list (exact, global phase included).
+std::vector<qs_gate> fold_rotations(int n, const qs_gate *in, size_t n_in);
 
 // Profile-guided selection (pgo.cpp).
 uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts &o, uint64_t base);

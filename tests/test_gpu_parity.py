@@ -28,6 +28,8 @@ FLAGS = {
     "diag": qs.QS_DIAG,
     "pgo_rules": qs.QS_PGO_RULES,
     "pgo_measured": qs.QS_PGO_MEASURED,
+    "fold_vswap_k4_diag": qs.QS_FOLD | qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_DIAG,
+    "fold_plain": qs.QS_FOLD,
     **{f"vswap_k{k}": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) for k in range(1, 7)},
     **{f"vswap_k{k}_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)},
     **{f"vswap_k{k}_tc": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC for k in (4, 5, 6)},
@@ -60,6 +62,8 @@ def check(n, gates, flags, dtype, init=None):
     want, operm = oracle.simulate(text, init=init)
     got, perm = gpu_run(n, qs.gates_to_array(gates), flags, dtype, init=init)
     pgo = qs.QS_PGO_RULES | qs.QS_PGO_MEASURED
+    if flags & qs.QS_FOLD and not flags & (qs.QS_VSWAP | pgo):
+        pass  # folding may cancel SWAP pairs; without virtual swap perm stays identity
     if flags & (qs.QS_VSWAP | pgo) and any(g[0] == "swap" for g in gates):
         if flags & qs.QS_PGO_MEASURED and list(perm) == list(range(n)):
             pass  # the measured activator may choose a plan without virtual swap
