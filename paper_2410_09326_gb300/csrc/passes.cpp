@@ -313,6 +313,58 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     pg.push_back(g);
   }
 
+  // (1b) relocation (Sec. III-D: move hot qubits out of the slow segment).
+  // Here the slow positions are physical bits 0 and 1: a block whose targets
+  // include both gathers 8-byte elements at 32-byte strides. When the share
+  // of multi-qubit non-diagonal gates touching them exceeds reloc_share and
+  // twice the share a random qubit pair would have, each
+  // hot low bit is exchanged once, up front, with the high bit that carries
+  // the fewest such gates, and every gate is renamed.
+  std::vector<std::pair<int, int>> reloc;
+  if ((flags & QS_RELOCATE) && n >= 6) {
+    std::vector<double> heat(64, 0.0);
+    double total = 0, low = 0;
+    for (const qs_gate &g : pg) {
+      if (op_info(g.op).diagonal || g.nq < 2) continue;
+      total += 1;
+      bool touches_low = false;
+      for (int j = 0; j < g.nq; j++) {
+        heat[g.q[j]] += 1;
+        touches_low |= g.q[j] < 2;
+      }
+      if (touches_low) low += 1;
+    }
+    // "hot" means well above the share a random pair of qubits would have
+    const double uniform = 1.0 - (double)(n - 2) * (n - 3) / ((double)n * (n - 1));
+    if (total > 0 && low / total > std::max(opts.reloc_share, 2.0 * uniform)) {
+      std::vector<int> used;
+      for (int lowq = 0; lowq < 2; lowq++) {
+        if (heat[lowq] == 0) continue;
+        int best = -1;
+        for (int q = n - 1; q >= 5; q--) {
+          if (std::find(used.begin(), used.end(), q) != used.end()) continue;
+          if (best < 0 || heat[q] < heat[best]) best = q;
+        }
+        if (best < 0 || heat[best] >= heat[lowq]) continue;
+        used.push_back(best);
+        reloc.push_back({lowq, best});
+      }
+      for (auto &pr : reloc) {
+        const int a = pr.first, b = pr.second;
+        for (qs_gate &g : pg)
+          for (int j = 0; j < g.nq; j++) {
+            if (g.q[j] == a) g.q[j] = (uint8_t)b;
+            else if (g.q[j] == b) g.q[j] = (uint8_t)a;
+          }
+        for (int l = 0; l < n; l++) {
+          if (perm[l] == a) perm[l] = (int8_t)b;
+          else if (perm[l] == b) perm[l] = (int8_t)a;
+        }
+      }
+      stats.relocations = (int)reloc.size();
+    }
+  }
+
   // (2) grouping
   std::vector<Pending> groups;
   if (!fuse && !dfuse) {
@@ -370,7 +422,17 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   parallel_for(groups.size(), [&](size_t i) {
     if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i]) ? 1 : 0;
   });
-  plan.reserve(groups.size());
+  plan.reserve(groups.size() + reloc.size());
+  for (auto &pr : reloc) {  // the exchanges run first
+    Block b;
+    b.kind = BK_PERMUTE;
+    b.k = 2;
+    b.q[0] = std::min(pr.first, pr.second);
+    b.q[1] = std::max(pr.first, pr.second);
+    b.n_gates = 0;
+    b.meta = 3;
+    plan.push_back(std::move(b));
+  }
   for (size_t i = 0; i < groups.size(); i++)
     if (keep[i]) plan.push_back(std::move(done[i]));
   for (Block &b : plan)

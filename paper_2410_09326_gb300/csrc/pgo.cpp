@@ -92,12 +92,15 @@ uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts
     }
   }
   (void)n;
-  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_FOLD | (15ull << 16));
+  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_FOLD | QS_RELOCATE | (15ull << 16));
   // rotation folding: T gates above the threshold share of all gates
   if (n_gates && (double)t_count / (double)n_gates > o.t_ratio) f |= QS_FOLD;
   // virtual swap: SWAP gates present, or two-qubit gates hitting the fast
   // segment (the paper's CPhase/CNOT counter rule)
   if (swaps > 0 || two_q_low > 0) f |= QS_VSWAP;
+  // relocation: the planner moves bits 0 and 1 out of the way when their
+  // share of multi-qubit gates passes opts.reloc_share
+  if (two_q_low > 0) f |= QS_RELOCATE;
   // merging: a run of consecutive one-qubit gates above the threshold, or
   // (GPU reading) any circuit with more than one gate, since each fused gate
   // saves a full pass over the state

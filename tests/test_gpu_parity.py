@@ -30,6 +30,7 @@ FLAGS = {
     "pgo_measured": qs.QS_PGO_MEASURED,
     "fold_vswap_k4_diag": qs.QS_FOLD | qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_DIAG,
     "fold_plain": qs.QS_FOLD,
+    "relocate_k4_tc": qs.QS_RELOCATE | qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_TC | qs.QS_DIAG,
     **{f"vswap_k{k}": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) for k in range(1, 7)},
     **{f"vswap_k{k}_diag": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)},
     **{f"vswap_k{k}_tc": qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC for k in (4, 5, 6)},
@@ -61,12 +62,12 @@ def check(n, gates, flags, dtype, init=None):
     text = cg.to_qasm(n, gates)
     want, operm = oracle.simulate(text, init=init)
     got, perm = gpu_run(n, qs.gates_to_array(gates), flags, dtype, init=init)
-    pgo = qs.QS_PGO_RULES | qs.QS_PGO_MEASURED
+    pgo = qs.QS_PGO_RULES | qs.QS_PGO_MEASURED | qs.QS_RELOCATE
     if flags & qs.QS_FOLD and not flags & (qs.QS_VSWAP | pgo):
         pass  # folding may cancel SWAP pairs; without virtual swap perm stays identity
     if flags & (qs.QS_VSWAP | pgo) and any(g[0] == "swap" for g in gates):
-        if flags & qs.QS_PGO_MEASURED and list(perm) == list(range(n)):
-            pass  # the measured activator may choose a plan without virtual swap
+        if flags & (qs.QS_PGO_MEASURED | qs.QS_RELOCATE | qs.QS_PGO_RULES):
+            pass  # relocation (or a plan without virtual swap) changes the map
         else:
             assert list(perm) == list(operm), (list(perm), list(operm))
     elif not flags & (qs.QS_VSWAP | pgo):
@@ -170,6 +171,29 @@ def test_config1_random_n20_vs_oracle():
     n, gates = c["random"]
     for name in ("plain", "vswap", "vswap_k3_diag", "vswap_k5_diag", "vswap_k4_tc_diag", "vswap_k5_tc_diag"):
         check(n, gates, FLAGS[name], qs.QS_C64)
+
+
+def test_relocation_speeds_up_a_low_heavy_circuit():
+    """Blocks whose targets include bits 0 and 1 gather at a 32-byte stride;
+    moving those bits up front (two half-state exchanges) pays off."""
+    from tests.test_host import low_heavy_circuit
+    n = 26
+    gates = low_heavy_circuit(n, reps=60, seed=5, swaps=False)
+    arr = qs.gates_to_array(gates)
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        t = {}
+        for name, f in (("base", FLAGS["vswap_k4_tc"]), ("reloc", FLAGS["vswap_k4_tc"] | qs.QS_RELOCATE)):
+            best = 1e9
+            for _ in range(3):
+                qs.qs_set_basis(st, 0)
+                qs.qs_apply_circuit(st, arr, f | qs.QS_PROFILE)
+                summ, _ = qs.qs_profile(st, with_records=False)
+                best = min(best, summ.total_ms)
+            t[name] = best
+        assert t["reloc"] < t["base"], t
+    finally:
+        qs.qs_free_state(st)
 
 
 def test_tc_blocks_really_run_on_tensor_cores():

@@ -132,8 +132,10 @@ def test_plan_reproduces_oracle_all_gate_types(flags):
     gates = cg.all_gate_types_circuit(n, 250, rng)
     want, operm = oracle.simulate(cg.to_qasm(n, gates))
     got, perm, recs = plan_state(n, gates, flags)
-    if flags & qs.QS_VSWAP or flags & qs.QS_PGO_RULES:
+    if flags & qs.QS_VSWAP:
         assert list(perm) == list(operm)
+    elif flags & qs.QS_PGO_RULES:
+        assert sorted(perm) == list(range(n))  # the rules may also relocate
     else:
         assert list(perm) == list(range(n))
     assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
@@ -285,3 +287,38 @@ def test_measured_select_follows_the_table():
             t.bytes[cls] = 7000.0 * 1e6
     flags, _ = qs.qs_pgo_select(n, arr, table=t)
     assert (flags >> 16) & 15 == 6 and not flags & qs.QS_TC
+
+
+def low_heavy_circuit(n, reps=30, seed=3, swaps=True):
+    rng = cg.SplitMix64(seed)
+    gates = []
+    for _ in range(reps):
+        gates.append(("u3", [0], [rng.uniform(0, 6) for _ in range(3)]))
+        gates.append(("u3", [1], [rng.uniform(0, 6) for _ in range(3)]))
+        gates.append(("cx", [0, 1]))
+        gates.append(("cx", [1, 2 + rng.randint(n - 2)]))
+        if swaps:
+            gates.append(("swap", [2 + rng.randint(n - 2), 2 + rng.randint(n - 2)]))
+            if gates[-1][1][0] == gates[-1][1][1]:
+                gates.pop()
+    return gates
+
+
+@pytest.mark.parametrize("flags", [qs.QS_RELOCATE, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_RELOCATE,
+                                   qs.QS_PGO_RULES])
+def test_relocation_moves_hot_low_bits_and_stays_exact(flags):
+    n = 14
+    gates = low_heavy_circuit(n)
+    want, _ = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, recs = plan_state(n, gates, flags)
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+    exchanges = [r for r in recs if r.kind == 2 and r.n_gates == 0]
+    assert len(exchanges) == 2 and {min(r.qubits[0], r.qubits[1]) for r in exchanges} == {0, 1}
+    # after relocation no dense block targets both bits 0 and 1
+    assert not any(r.kind == 0 and r.k >= 2 and r.qubits[0] == 0 and r.qubits[1] == 1 for r in recs)
+
+
+def test_relocation_leaves_balanced_circuits_alone():
+    n, gates = cg.config0_circuit(0)
+    recs, _, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_RELOCATE)
+    assert not any(r.kind == 2 and r.n_gates == 0 for r in recs)
