@@ -290,7 +290,7 @@ def run_ours(args):
 # scaled to n=30 by the amplitudes processed (profiles/k_dense_tc5_n26.md,
 # profiles/k_diag_chunk_n26.md: 1012.3 / 1012.2 MB at n=26 -> x16); absent
 # where no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {"k_dense_k5_tc": 16.20e9, "k_diag": 16.19e9}
+TRAFFIC_PER_LAUNCH = {"k_diag": 16.19e9}
 
 
 # ---------------------------------------------------------------------------
@@ -369,7 +369,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-CASES = ("tc5", "tc4", "dense3", "diag10", "permute", "probs")
+CASES = ("tc6", "tc5", "tc4", "dense3", "diag10", "permute", "probs")
 
 
 def run_case(args):
@@ -380,9 +380,11 @@ def run_case(args):
     qs.load(build_if_missing=True)
     n = args.n
     rng = cg.SplitMix64(77)
-    k = {"tc5": 5, "tc4": 4, "dense3": 3}.get(args.case, 0)
+    k = {"tc6": 6, "tc5": 5, "tc4": 4, "dense3": 3}.get(args.case, 0)
+    opts = qs.qs_default_opts()
+    opts.tc_precision = args.tc_precision
     if k:
-        qubits = [1, 6, 11, 16, 21][:k] if n > 21 else list(range(0, 2 * k, 2))
+        qubits = [1, 6, 11, 16, 21, 24][:k] if n > 24 else list(range(0, 2 * k, 2))
         if args.targets:
             qubits = [int(x) for x in args.targets.split(",")]
         gates = [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
@@ -404,7 +406,7 @@ def run_case(args):
         if args.case == "probs":
             qs.qs_measure_probs(st, list(range(10)))
         else:
-            qs.qs_apply_circuit(st, arr, flags | qs.QS_PROFILE)
+            qs.qs_apply_circuit(st, arr, flags | qs.QS_PROFILE, opts)
     if args.case != "probs":
         summ, recs = qs.qs_profile(st)
         print(json.dumps({"case": args.case, "n": n, "blocks": [(kernel_name(r), round(r.ms, 4),
@@ -572,6 +574,7 @@ def main():
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
+    ap.add_argument("--tc-precision", type=int, default=0, help="tensor-core operands: 0 two FP16 halves, 1 3xTF32")
     ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32"],
                     help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
     ap.add_argument("--train-circuits", type=int, default=60)

@@ -87,7 +87,7 @@ typedef struct {
 #define QS_VSWAP ((uint64_t)1 << 0)         /* SWAPs become relabellings of perm */
 #define QS_FUSE ((uint64_t)1 << 1)          /* k-qubit fusion, k from QS_FUSE_K */
 #define QS_DIAG ((uint64_t)1 << 2)          /* diagonal runs fuse up to QS_MAX_DIAG wide */
-#define QS_TC ((uint64_t)1 << 3)            /* dense k>=4 blocks on tensor cores */
+#define QS_TC ((uint64_t)1 << 3)            /* dense k>=4 blocks on tensor cores (opts->tc_precision) */
 #define QS_PROFILE ((uint64_t)1 << 4)       /* time every block with CUDA events */
 #define QS_RELOCATE ((uint64_t)1 << 5)      /* profile-guided hot-qubit relocation */
 #define QS_FOLD ((uint64_t)1 << 6)          /* rotation folding + pair cancellation first */
@@ -105,7 +105,8 @@ typedef struct {
   int diag_max;         /* widest diagonal block, 1..QS_MAX_DIAG */
   int threads;          /* launch override: threads per CTA (0 = tuned default) */
   double peak_gbs;      /* HBM copy bandwidth the cost model scales its priors by */
-  int reserved[6];
+  int tc_precision;     /* QS_TC operands: 0 = two FP16 halves (k = 4..6), 1 = 3 x TF32 (k = 4, 5) */
+  int reserved[5];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

@@ -327,13 +327,14 @@ bool block_needs_dev_matrix(const Block &b, bool c128) {
 
 size_t block_dev_matrix_bytes(const Block &b, bool c128) {
   if (!block_needs_dev_matrix(b, c128)) return 0;
-  if (b.tc && !c128) return tc_b_floats(b.k) * sizeof(float);
+  if (b.tc && !c128) return b.tc_tf32 ? tc_b_floats(b.k) * sizeof(float) : tc16_b_bytes(b.k);
   return b.mat.size() * (c128 ? 16 : 8);
 }
 
 void fill_dev_matrix(const Block &b, bool c128, void *host_out) {
   if (b.tc && !c128) {
-    tc_build_b(b, (float *)host_out);
+    if (b.tc_tf32) tc_build_b(b, (float *)host_out);
+    else tc16_build_b(b, host_out);
     return;
   }
   for (size_t k = 0; k < b.mat.size(); k++) {
@@ -350,7 +351,9 @@ void fill_dev_matrix(const Block &b, bool c128, void *host_out) {
 cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
                                      int *err, cudaStream_t s, int threads) {
   if (threads <= 0) threads = 256;
-  if (b.kind == BK_DENSE && b.tc && !c128) return run_dense_tc((float2 *)amps, n, b, dev_mat, err, s);
+  if (b.kind == BK_DENSE && b.tc && !c128)
+    return b.tc_tf32 ? run_dense_tc((float2 *)amps, n, b, dev_mat, err, s)
+                     : run_dense_tc16((float2 *)amps, n, b, dev_mat, err, s);
   if (c128) return run_block<double2>((double2 *)amps, n, b, dev_mat, s, threads);
   return run_block<float2>((float2 *)amps, n, b, dev_mat, s, threads);
 }

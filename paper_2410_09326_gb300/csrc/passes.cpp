@@ -435,8 +435,11 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   }
   for (size_t i = 0; i < groups.size(); i++)
     if (keep[i]) plan.push_back(std::move(done[i]));
-  for (Block &b : plan)
-    b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= 5;
+  const bool tf32 = opts.tc_precision == 1;
+  for (Block &b : plan) {
+    b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= (tf32 ? 5 : 6);
+    b.tc_tf32 = b.tc && tf32;
+  }
   return QS_OK;
 }
 

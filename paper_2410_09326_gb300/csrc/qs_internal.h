@@ -56,6 +56,7 @@ struct Block {
   int first_op = -1;              // op of a single-gate block
   int meta = 4;                   // 0 one-qubit, 1 two-qubit, 3 swap, 4 fused
   bool tc = false;
+  bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
 };
 
 struct PlanStats {

@@ -1,0 +1,334 @@
+// Dense fused blocks on the tensor cores with FP16 operands (tcgen05
+// kind::f16, FP32 accumulation), K = 4, 5, 6 targets.
+//
+// Same real GEMM as the TF32 kernel (tc_dense.cu): group m of a 128-group
+// tile is row m of A (its 2^K amplitudes as interleaved re/im, K-major), the
+// real embedding of the block matrix is B, D = A B^T lands in TMEM with lane
+// m = group m. Operands are split in two FP16 halves, hi = fp16(x) and
+// lo = fp16(x - hi), each with an 11-bit significand, and
+// D = A_hi B_hi + A_hi B_lo + A_lo B_hi keeps ~22 bits of the product (the
+// same as 3 x TF32, at twice the tensor rate and half the shared memory).
+// FP16's range is narrow: every row of A is scaled by a power of two so its
+// largest component lies in [0.5, 1) before the split. Matrix entries are at
+// most 1 in magnitude and need no scaling. In the epilogue the large and the
+// small products (kept in separate TMEM columns, because the accumulation
+// rounds toward zero) are summed in registers and each group is rescaled to
+// its input norm -- a fused block is unitary -- which also undoes the row
+// scale exactly.
+//
+// Shared memory per CTA: A hi/lo 2 x 128 x 2^(K+1) x 2 B and B hi/lo
+// 2 x 4^(K+1) x 2 B: 20 KB (K=4), 48 KB (K=5), 128 KB (K=6).
+#include <cstdint>
+#include <cstring>
+
+#include <cuda_fp16.h>
+
+#include "tc_common.cuh"
+
+namespace qs {
+namespace kern {
+
+namespace {
+
+// kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = F16
+// (format 0 in bits 7-9 and 10-12), both K-major, N >> 3 in bits 17-22,
+// M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Resident CTAs per SM the register budget is sized for.
+template <int K> struct Tc16Occ {
+  static constexpr int value = K <= 4 ? 4 : (K == 5 ? 3 : 1);
+};
+
+template <int K>
+__global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
+    k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
+                 int *__restrict__ err) {
+  constexpr int D = 1 << K;                    // amplitudes per group
+  constexpr int KR = 2 * D;                    // real K = N of the GEMM
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;    // 8-row groups (both operands)
+  constexpr uint32_t LBO = 128u;               // K-adjacent core matrices
+  constexpr uint32_t NCOLS = 2 * KR;           // large and small accumulators
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA_hi = smem;
+  unsigned char *sA_lo = smem + A_BYTES;
+  unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t mbar_a = smem_addr(&mbar);
+  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+
+  uint64_t d[K];
+#pragma unroll
+  for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
+  const bool pair = p.tq[0] == 0;
+  // this thread's row of A: 8-row group (tid / 8), row (tid % 8) of each core matrix
+  const uint32_t row_off = (uint32_t)(tid >> 3) * SBO + (uint32_t)(tid & 7) * 16u;
+  uint32_t phase = 0;
+  bool aborted = false;
+
+  long long tile = blockIdx.x;
+  float2 v[D];
+  uint64_t base = 0;
+  bool valid = false;
+  auto gather = [&](long long t, uint64_t &b, bool &ok) {
+    const long long g = t * kTcThreads + tid;
+    ok = t < p.n_tiles && g < p.n_groups;
+    b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
+    if (pair) {
+#pragma unroll
+      for (int s = 0; s < D; s += 2) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int j = 1; j < K; j++)
+          if ((s >> j) & 1) off += d[j];
+        const float4 x = ok ? *reinterpret_cast<const float4 *>(a + b + off) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[s] = make_float2(x.x, x.y);
+        v[s + 1] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < D; s++) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+          if ((s >> j) & 1) off += d[j];
+        v[s] = ok ? a[b + off] : make_float2(0.f, 0.f);
+      }
+    }
+  };
+  auto store = [&](uint64_t b, int s, float re, float im) {
+    uint64_t off = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++)
+      if ((s >> j) & 1) off += d[j];
+    a[b + off] = make_float2(re, im);
+  };
+  gather(tile, base, valid);
+
+  for (; tile < p.n_tiles; tile += gridDim.x) {
+    // row scale: largest component into [0.5, 1)
+    float mx = 0.f, nin = 0.f;
+#pragma unroll
+    for (int s = 0; s < D; s++) {
+      mx = fmaxf(mx, fmaxf(fabsf(v[s].x), fabsf(v[s].y)));
+      nin = fmaf(v[s].x, v[s].x, fmaf(v[s].y, v[s].y, nin));
+    }
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+    // hi/lo rows: amplitudes 4c..4c+3 fill the 16-byte row of core matrix c
+#pragma unroll
+    for (int c = 0; c < D / 4; c++) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        x[2 * u] = v[4 * c + u].x * sc;
+        x[2 * u + 1] = v[4 * c + u].y * sc;
+      }
+      uint4 hi, lo;
+      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const __half2 h = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+        const float2 hf = __half22float2(h);
+        hp[u] = *reinterpret_cast<const uint32_t *>(&h);
+        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
+      *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ks++) {
+        const uint32_t koff = (uint32_t)ks * 2u * LBO;
+        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+        mma_f16(tmem, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
+        mma_f16(tmem + KR, dah, dbl, IDESC, ks > 0 ? 1u : 0u);
+        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+      }
+      mma_commit(mbar_a);
+    }
+    const uint64_t cur_base = base;
+    const bool cur_valid = valid;
+    gather(tile + gridDim.x, base, valid);  // next tile, in flight during the MMAs
+    const bool ok = mbar_wait(mbar_a, phase);
+    phase ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      aborted = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    // pass 1: norm of the computed group (large + small products), 16
+    // columns (8 amplitudes) at a time to keep registers free
+    float nout = 0.f;
+#pragma unroll
+    for (int h = 0; h < KR / 16; h++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * h, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    // unitary block: the group keeps its input norm (this also undoes the row scale)
+    const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+    // pass 2: scale and store, 8 amplitudes per chunk
+#pragma unroll
+    for (int h = 0; h < KR / 16; h++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * h, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (cur_valid) {
+        if (pair) {
+#pragma unroll
+          for (int u = 0; u < 4; u++) {
+            const int s = 8 * h + 2 * u;
+            uint64_t off = 0;
+#pragma unroll
+            for (int j = 1; j < K; j++)
+              if ((s >> j) & 1) off += d[j];
+            float y[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) y[q] = (__uint_as_float(rb[4 * u + q]) + __uint_as_float(rs[4 * u + q])) * f;
+            *reinterpret_cast<float4 *>(a + cur_base + off) = make_float4(y[0], y[1], y[2], y[3]);
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; u++)
+            store(cur_base, 8 * h + u, (__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
+                  (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) mbar_wait(mbar_a, phase ^ 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+template <int K> size_t tc16_smem_bytes() {
+  constexpr size_t KR = 2 << K;
+  return 2 * 128 * KR * 2 + 2 * KR * KR * 2;
+}
+
+template <int K>
+cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+  TcParam p;
+  p.n_groups = 1ll << (n - K - b.nctrl);
+  p.n_tiles = (p.n_groups + kTcThreads - 1) / kTcThreads;
+  p.cmask = b.cmask;
+  fill_fixed(b, p.fixed, p.nf);
+  for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
+  const size_t smem = tc16_smem_bytes<K>();
+  // per device: opt in to the shared memory and size one wave of resident
+  // CTAs; TMEM columns stay within 512 per SM (4 x 64, 3 x 128, 1 x 256)
+  static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc16<K>, kTcThreads, smem);
+    per_sm = occ > Tc16Occ<K>::value ? Tc16Occ<K>::value : occ;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms * per_sm;
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16<K><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc16_b_bytes(int k) { return 2u * (size_t)(2 << k) * (size_t)(2 << k) * 2u; }
+
+// B = real embedding of U, split into FP16 hi/lo, in the 16-bit core-matrix
+// layout (row r, column c at (r/8) * (KR/8) * 64 + (c/8) * 64 + (r%8) * 8 + c%8 halves).
+void tc16_build_b(const Block &b, void *out) {
+  const int D = 1 << b.k, KR = 2 * D;
+  const size_t n = (size_t)KR * KR;
+  __half *h = (__half *)out;
+  auto at = [&](int row, int col) {
+    return (size_t)(row >> 3) * (KR / 8) * 64 + (size_t)(col >> 3) * 64 + (row & 7) * 8 + (col & 7);
+  };
+  for (int r = 0; r < D; r++)
+    for (int s = 0; s < D; s++) {
+      const cd u = b.mat[(size_t)r * D + s];
+      const float vals[2][2] = {{(float)u.real(), (float)-u.imag()}, {(float)u.imag(), (float)u.real()}};
+      for (int i = 0; i < 2; i++)
+        for (int j = 0; j < 2; j++) {
+          const float x = vals[i][j];
+          const __half hi = __float2half_rn(x);
+          const __half lo = __float2half_rn(x - __half2float(hi));
+          h[at(2 * r + i, 2 * s + j)] = hi;
+          h[n + at(2 * r + i, 2 * s + j)] = lo;
+        }
+    }
+}
+
+cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+  switch (b.k) {
+    case 4: return run_tc16<4>(a, n, b, dev_b, err, s);
+    case 5: return run_tc16<5>(a, n, b, dev_b, err, s);
+    case 6: return run_tc16<6>(a, n, b, dev_b, err, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace kern
+}  // namespace qs

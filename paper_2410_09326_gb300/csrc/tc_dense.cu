@@ -34,37 +34,17 @@
 #include <cstdint>
 #include <cstring>
 
-#include "kernels_common.cuh"
+#include "tc_common.cuh"
 
 namespace qs {
 namespace kern {
 
 namespace {
 
-constexpr int kTcThreads = 128;
-constexpr uint32_t kSpinLimit = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
 __device__ __forceinline__ float tf32_rn(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
-// start >> 4 in bits 0-13, leading-dimension (K-direction) byte offset >> 4
-// in bits 16-29, stride (M/N-direction) byte offset >> 4 in bits 32-45,
-// descriptor version 1 in bits 46-47, swizzle mode 0 in bits 61-63.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
 }
 
 // Instruction descriptor for kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -82,56 +62,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
 }
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpinLimit; i++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-template <int N> struct TmemLd;
-template <> struct TmemLd<32> {
-  __device__ static void run(uint32_t taddr, uint32_t *r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-  }
-};
-template <> struct TmemLd<64> {
-  __device__ static void run(uint32_t taddr, uint32_t *r) {
-    TmemLd<32>::run(taddr, r);
-    TmemLd<32>::run(taddr + 32, r + 32);
-  }
-};
-
-struct TcParam {
-  long long n_groups;
-  long long n_tiles;
-  unsigned long long cmask;
-  int nf;
-  int fixed[kMaxFixed];
-  int tq[QS_MAX_FUSE];
-};
 
 // K = targets (4 or 5). bmat: B_hi then B_lo, each N x N floats already in
 // the core-matrix layout (built on the host). err: error word (0 = fine).
