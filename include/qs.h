@@ -106,7 +106,10 @@ typedef struct {
   int threads;          /* launch override: threads per CTA (0 = tuned default) */
   double peak_gbs;      /* HBM copy bandwidth the cost model scales its priors by */
   int tc_precision;     /* QS_TC operands: 0 = two FP16 halves (k = 4..6), 1 = 3 x TF32 (k = 4, 5) */
-  int reserved[5];
+  int test_wait_timeout; /* test hook, 0 in normal use: tensor-core blocks withhold their
+                            completion signal, so their bounded (1 s) wait runs out and the
+                            next synchronising call returns QS_ETIMEOUT; results invalid */
+  int reserved[4];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

@@ -61,7 +61,8 @@ class qs_opts(ctypes.Structure):
     _fields_ = [("merge_run", ctypes.c_int), ("t_ratio", ctypes.c_double),
                 ("low_bits", ctypes.c_int), ("reloc_share", ctypes.c_double),
                 ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
-                ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
+                ("test_wait_timeout", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class qs_class_table(ctypes.Structure):

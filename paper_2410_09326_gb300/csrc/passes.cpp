@@ -439,6 +439,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   for (Block &b : plan) {
     b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= (tf32 ? 5 : 6);
     b.tc_tf32 = b.tc && tf32;
+    b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;
 }

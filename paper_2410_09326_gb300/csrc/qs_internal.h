@@ -57,6 +57,7 @@ struct Block {
   int meta = 4;                   // 0 one-qubit, 1 two-qubit, 3 swap, 4 fused
   bool tc = false;
   bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
+  bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
 };
 
 struct PlanStats {

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
         mma_f16(tmem + KR, dah, dbl, IDESC, ks > 0 ? 1u : 0u);
         mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
       }
-      mma_commit(mbar_a);
+      if (!p.withhold_commit) mma_commit(mbar_a);
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
@@ -256,7 +256,12 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (aborted) mbar_wait(mbar_a, phase ^ 1);
+  if (aborted) {
+    // MMAs may still be in flight: make sure their completion is signalled,
+    // give them a bounded chance to land, then return the columns
+    if (tid == 0) mma_commit(mbar_a);
+    mbar_wait(mbar_a, phase ^ 1);
+  }
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
@@ -271,6 +276,7 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   p.n_groups = 1ll << (n - K - b.nctrl);
   p.n_tiles = (p.n_groups + kTcThreads - 1) / kTcThreads;
   p.cmask = b.cmask;
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
   fill_fixed(b, p.fixed, p.nf);
   for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
   const size_t smem = tc16_smem_bytes<K>();

@@ -33,7 +33,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the mbarrier phase with the given parity; gives up after
+// kWaitLimitNs of wall time (or kSpinLimit polls) and returns false.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
   for (uint32_t i = 0; i < kSpinLimit; i++) {
     uint32_t done;
     asm volatile(
@@ -44,6 +54,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
         : "r"(mbar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitLimitNs) return false;
   }
   return false;
 }
@@ -85,6 +96,7 @@ struct TcParam {
   int nf;
   int fixed[kMaxFixed];
   int tq[QS_MAX_FUSE];
+  int withhold_commit;  // test hook: the MMA completion is not signalled, so the wait runs out
 };
 
 }  // namespace kern

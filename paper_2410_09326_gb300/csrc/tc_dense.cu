@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kTcThreads, TcOcc<K>::value)
           mma_tf32(tmem, dal, dbh, IDESC, 1u);
         }
       }
-      mma_commit(mbar_a);
+      if (!p.withhold_commit) mma_commit(mbar_a);
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
@@ -274,8 +274,9 @@ __global__ void __launch_bounds__(kTcThreads, TcOcc<K>::value)
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
-    // an MMA may still be in flight: give it a bounded chance to land
-    // before the columns are returned
+    // MMAs may still be in flight: make sure their completion is signalled,
+    // give them a bounded chance to land, then return the columns
+    if (tid == 0) mma_commit(mbar_a);
     mbar_wait(mbar_a, phase ^ 1);
   }
   if (warp == 0) {
@@ -328,6 +329,7 @@ cudaError_t run_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err
   p.n_groups = 1ll << (n - K - b.nctrl);
   p.n_tiles = (p.n_groups + kTcThreads - 1) / kTcThreads;
   p.cmask = b.cmask;
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
   fill_fixed(b, p.fixed, p.nf);
   for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
   const size_t smem = tc_smem_bytes<K>();

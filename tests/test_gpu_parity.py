@@ -319,6 +319,32 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
+def test_bounded_wait_times_out_and_state_recovers():
+    """Failure detection without a GPU fault: the test hook withholds the
+    tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
+    frees its TMEM and returns, and the next synchronising call reports
+    QS_ETIMEOUT. The state stays usable."""
+    n = 14
+    gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(5)] + [("cx", [0, 1]), ("cx", [2, 3]), ("cx", [3, 4])]
+    arr = qs.gates_to_array(gates)
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        opts = qs.qs_default_opts()
+        opts.test_wait_timeout = 1
+        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_TC, opts)
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_norm(st)
+        assert e.value.status == qs.QS_ETIMEOUT
+        # the error is reported once; the state can be reset and used again
+        qs.qs_set_basis(st, 0)
+        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_TC)
+        want, _ = oracle.simulate(cg.to_qasm(n, gates))
+        got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        assert np.linalg.norm(got - want) < 1e-5
+    finally:
+        qs.qs_free_state(st)
+
+
 def test_attach_torch_tensor_and_stream():
     torch = pytest.importorskip("torch")
     n = 12
