@@ -91,6 +91,9 @@ typedef struct {
 #define QS_PROFILE ((uint64_t)1 << 4)       /* time every block with CUDA events */
 #define QS_RELOCATE ((uint64_t)1 << 5)      /* profile-guided hot-qubit relocation */
 #define QS_FOLD ((uint64_t)1 << 6)          /* rotation folding + pair cancellation first */
+#define QS_TILE ((uint64_t)1 << 7)          /* cache-blocked passes: runs of blocks whose targets fit one
+                                               shared-memory tile (opts->tile_bits qubits, the lowest
+                                               bits included) share one HBM pass */
 #define QS_PGO_RULES ((uint64_t)1 << 8)     /* pick flags with the paper's counter rules */
 #define QS_PGO_MEASURED ((uint64_t)1 << 9)  /* pick flags from a measured block profile */
 #define QS_FUSE_K(k) ((uint64_t)((k) & 15) << 16)
@@ -109,7 +112,10 @@ typedef struct {
   int test_wait_timeout; /* test hook, 0 in normal use: tensor-core blocks withhold their
                             completion signal, so their bounded (1 s) wait runs out and the
                             next synchronising call returns QS_ETIMEOUT; results invalid */
-  int reserved[4];
+  int tile_bits;        /* QS_TILE: qubits per shared-memory tile, 0 = 64 KiB of amplitudes
+                           (13 for c64, 12 for c128); 8..14 c64, 8..13 c128 */
+  int tile_k;           /* QS_TILE: fusion width inside a tile, 0 = 3; 1..4 */
+  int reserved[2];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);
@@ -156,6 +162,10 @@ qs_status qs_parse_qasm(const char *text, int *n_qubits, qs_gate *gates, size_t 
  * qubits, commuting gates past each other only where they act diagonally on
  * every shared qubit; QS_DIAG lets diagonal runs grow to opts->diag_max
  * qubits; QS_TC runs dense blocks with 4..6 targets on the tensor cores;
+ * QS_TILE groups gates (same commutation rule) into passes whose non-diagonal
+ * qubits fit a tile of opts->tile_bits qubits and applies each pass -- its
+ * gates fused again, at most opts->tile_k wide -- in shared memory during one
+ * read and one write of the state (QS_TILE is ignored when n <= tile bits);
  * QS_PGO_RULES / QS_PGO_MEASURED replace the pass flags by the activator's
  * choice (see qs_pgo_select). gates is copied during the call; the launches
  * are asynchronous on the state's stream.
@@ -175,12 +185,16 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
  */
 typedef struct {
   int32_t index;     /* launch order within the last apply call */
-  uint8_t kind;      /* 0 dense block, 1 diagonal block, 2 physical bit exchange */
-  uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) */
+  uint8_t kind;      /* 0 dense block, 1 diagonal block, 2 physical bit exchange,
+                        3 tile pass (QS_TILE: several blocks in one HBM pass) */
+  uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) /
+                        tile qubits (tile pass) */
   uint8_t nctrl;     /* control bits that must be 1: only 2^(n-nctrl) amplitudes move */
   uint8_t tc;        /* 1 if it ran on the tensor cores */
-  int8_t qubits[QS_MAX_DIAG]; /* physical qubits ascending, -1 padded */
-  uint8_t meta;      /* 0 one-qubit gate, 1 two-qubit gate, 3 swap, 4 fused block */
+  int8_t qubits[QS_MAX_DIAG]; /* physical qubits ascending, -1 padded; for a tile pass the
+                                 tile's qubits above its contiguous low bits */
+  uint8_t meta;      /* 0 one-qubit gate, 1 two-qubit gate, 3 swap, 4 fused block,
+                        5 tile pass */
   uint8_t op;        /* qs_op of a single-gate block, 255 for a fused block */
   int32_t n_gates;   /* gates merged into the block */
   uint64_t cmask;    /* physical control bits (the block acts where all are 1) */
@@ -251,7 +265,10 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
  * as interleaved (re, im) pairs, block after block: (2^k)^2 entries for a
  * dense block (row-major over the block's ascending physical qubits, local
  * index sum_j bit(q_j) << j), 2^k phases for a diagonal block, none for an
- * exchange. *n_blocks and *mats_len (complex entries) receive the totals.
+ * exchange or a tile pass. A tile pass's record is followed by the records
+ * (and matrices) of its member blocks in the order the pass applies them;
+ * they carry the pass's index. *n_blocks (records) and *mats_len (complex
+ * entries) receive the totals.
  */
 qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, const qs_opts *opts,
                   int8_t *perm_inout, qs_block_record *recs, size_t cap, size_t *n_blocks,

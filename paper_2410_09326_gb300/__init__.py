@@ -27,6 +27,7 @@ QS_TC = 1 << 3
 QS_PROFILE = 1 << 4
 QS_RELOCATE = 1 << 5
 QS_FOLD = 1 << 6
+QS_TILE = 1 << 7
 QS_PGO_RULES = 1 << 8
 QS_PGO_MEASURED = 1 << 9
 
@@ -62,7 +63,8 @@ class qs_opts(ctypes.Structure):
                 ("low_bits", ctypes.c_int), ("reloc_share", ctypes.c_double),
                 ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
                 ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
-                ("test_wait_timeout", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
+                ("tile_k", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class qs_class_table(ctypes.Structure):

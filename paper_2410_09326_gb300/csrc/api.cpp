@@ -311,7 +311,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   std::string err;
   int8_t perm[QS_MAX_QUBITS];
   std::memcpy(perm, st->perm, sizeof(perm));
-  s = build_plan(st->n, gates, n_gates, flags, o, perm, plan, stats, err);
+  s = build_plan(st->n, gates, n_gates, flags, o, perm, plan, stats, err, st->dtype == QS_C128);
   if (s != QS_OK) return fail(s, "qs_apply_circuit: " + err);
   record_counters(st, gates, n_gates);
 
@@ -525,10 +525,10 @@ qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, c
   qs_status s = build_plan(n, gates, n_gates, flags, o, perm, plan, stats, err);
   if (s != QS_OK) return fail(s, "qs_plan: " + err);
   std::memcpy(perm_inout, perm, n);
-  size_t mlen = 0;
-  for (size_t i = 0; i < plan.size(); i++) {
-    const Block &b = plan[i];
-    if (recs && i < cap) fill_record(b, (int)i, n, 8, recs[i]);
+  size_t mlen = 0, nr = 0;
+  auto emit = [&](const Block &b, int index) {
+    if (recs && nr < cap) fill_record(b, index, n, 8, recs[nr]);
+    nr++;
     for (const cd &z : b.mat) {
       if (mats && mlen < mats_cap) {
         mats[2 * mlen] = z.real();
@@ -536,8 +536,12 @@ qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, c
       }
       mlen++;
     }
+  };
+  for (size_t i = 0; i < plan.size(); i++) {
+    emit(plan[i], (int)i);
+    for (const Block &m : plan[i].sub) emit(m, (int)i);  // a tile pass's members, in order
   }
-  if (n_blocks) *n_blocks = plan.size();
+  if (n_blocks) *n_blocks = nr;
   if (mats_len) *mats_len = mlen;
   return QS_OK;
 }

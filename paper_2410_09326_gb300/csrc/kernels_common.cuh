@@ -211,6 +211,13 @@ size_t tc16_b_bytes(int k);
 void tc16_build_b(const Block &b, void *out);
 cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s);
 
+// Cache-blocked passes (tile.cu): a BK_TILE block's descriptor (header,
+// member matrices and tables, member descriptors) lives in device memory.
+size_t tile_desc_bytes(const Block &b, bool c128);
+size_t tile_smem_bytes(const Block &b, bool c128);
+void tile_fill_desc(const Block &b, bool c128, void *out);
+cudaError_t run_tile(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s);
+
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 cudaError_t run_dense_c128(double2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 

@@ -88,7 +88,80 @@ struct Pending {
   std::vector<int> members;  // indices into the physical gate list
   uint64_t qmask = 0;
   bool all_diag = true;
+  uint64_t tmask = 0;       // qubits some member acts on non-diagonally
+  uint64_t out_union = 0;   // tile sub-groups: member qubits outside the tile
+  uint64_t cl_and = ~0ull;  // tile sub-groups: qubits every member is the identity on when 0
 };
+
+// Commuting greedy grouping of the gates pg[idx[..]] (ascending list order):
+// a gate may join any group at or after the last group it cannot commute
+// past (two gates commute when both act diagonally on every qubit they
+// share); it joins the first such group `fits` accepts, else a new one.
+struct NoJoin {
+  void operator()(Pending &, int, uint64_t) const {}
+};
+
+template <typename Fits, typename Joined = NoJoin>
+void greedy_groups(const std::vector<qs_gate> &pg, const std::vector<int> &idx, std::vector<Pending> &groups,
+                   Fits fits, Joined joined = Joined()) {
+  std::vector<int> last_any(64, -1), last_nd(64, -1);
+  for (int i : idx) {
+    const qs_gate &g = pg[i];
+    uint64_t gmask = 0, gt = 0;
+    int lower = -1;
+    for (int j = 0; j < g.nq; j++) {
+      const int q = g.q[j];
+      gmask |= 1ull << q;
+      if (!gate_diag_on(g, j)) gt |= 1ull << q;
+      lower = std::max(lower, gate_diag_on(g, j) ? last_nd[q] : last_any[q]);
+    }
+    const bool gdiag = op_info(g.op).diagonal;
+    int chosen = -1;
+    for (int b = std::max(lower, 0); b < (int)groups.size(); b++)
+      if (fits(groups[b], i, gmask, gt, gdiag)) {
+        chosen = b;
+        break;
+      }
+    if (chosen < 0) {
+      groups.emplace_back();
+      chosen = (int)groups.size() - 1;
+    }
+    Pending &p = groups[chosen];
+    p.members.push_back(i);
+    p.qmask |= gmask;
+    p.tmask |= gt;
+    p.all_diag = p.all_diag && gdiag;
+    joined(p, i, gmask);
+    for (int j = 0; j < g.nq; j++) {
+      const int q = g.q[j];
+      last_any[q] = std::max(last_any[q], chosen);
+      if (!gate_diag_on(g, j)) last_nd[q] = std::max(last_nd[q], chosen);
+    }
+  }
+}
+
+// Qubits on which the gate is the identity whenever that qubit is 0 (the
+// controls of a controlled gate; both qubits of CZ / CPhase; the qubit of a
+// phase gate diag(1, e^{ia})). A block made only of such gates on a qubit has
+// that qubit as a detected control.
+uint64_t ctrl_like_mask(const qs_gate &g) {
+  const OpInfo &oi = op_info(g.op);
+  uint64_t m = 0;
+  if (!oi.diagonal) {
+    for (int j = 0; j < oi.nctrl; j++) m |= 1ull << g.q[j];
+    return m;
+  }
+  std::vector<cd> G;
+  gate_full_matrix(g, G);
+  const int d = 1 << g.nq;
+  for (int j = 0; j < g.nq; j++) {
+    bool ok = true;
+    for (int l = 0; l < d && ok; l++)
+      if (!((l >> j) & 1) && !is_one(G[(size_t)l * d + l])) ok = false;
+    if (ok) m |= 1ull << g.q[j];
+  }
+  return m;
+}
 
 // Turns a group of gates into a classified Block (dense/diag/permute);
 // returns false when the product is the identity (nothing to launch).
@@ -218,9 +291,144 @@ bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_p
   return true;
 }
 
+void push_exchanges(const std::vector<std::pair<int, int>> &reloc, std::vector<Block> &plan) {
+  for (auto &pr : reloc) {  // the exchanges run first
+    Block b;
+    b.kind = BK_PERMUTE;
+    b.k = 2;
+    b.q[0] = std::min(pr.first, pr.second);
+    b.q[1] = std::max(pr.first, pr.second);
+    b.n_gates = 0;
+    b.meta = 3;
+    plan.push_back(std::move(b));
+  }
+}
+
+constexpr int kTileMaxOps = 64;     // member blocks of one tile pass
+constexpr int kTilePool = 2048;     // matrix + phase-table entries of one tile pass
+
+// Cache-blocked passes (the GPU analogue of the chunk segment that virtual
+// swap keeps hot qubits in, Sec. III-D): gates are grouped, with the same
+// commutation rule as fusion, into passes whose non-diagonal qubits fit one
+// tile of m qubits that always contains bits 0..kTileLowBits-1. A pass then
+// costs one HBM read and write: each CTA loads a tile of 2^m amplitudes
+// into shared memory, applies the pass's member blocks there, and stores it.
+// Inside a pass the gates are fused again, at most tile_k qubits wide; a
+// qubit outside the tile may only be a control or sit in a diagonal block.
+qs_status tile_plan(int n, const std::vector<qs_gate> &pg, const std::vector<int> &all, const qs_opts &opts,
+                    bool c128, std::vector<Block> &out, std::string &err) {
+  const int m = tile_bits_of(opts, c128);
+  const int kin = tile_k_of(opts);
+  const int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+  const uint64_t low = (1ull << kTileLowBits) - 1;
+  std::vector<Pending> passes;
+  greedy_groups(pg, all, passes, [&](const Pending &p, int, uint64_t, uint64_t gt, bool) {
+    return popcount64(p.tmask | low | gt) <= m;
+  });
+  // tile qubits of every pass: its non-diagonal qubits, padded with the
+  // lowest free bits (longer contiguous runs per load)
+  std::vector<uint64_t> tmask(passes.size());
+  for (size_t pi = 0; pi < passes.size(); pi++) {
+    uint64_t t = passes[pi].tmask | low;
+    for (int q = 0; q < n && popcount64(t) < m; q++) t |= 1ull << q;
+    tmask[pi] = t;
+  }
+  std::vector<uint64_t> cl(pg.size(), 0);
+  parallel_for(pg.size(), [&](size_t i) { cl[i] = ctrl_like_mask(pg[i]); });
+  // member blocks of every pass
+  std::vector<Pending> subs;
+  std::vector<int> sub_pass;
+  for (size_t pi = 0; pi < passes.size(); pi++) {
+    const uint64_t T = tmask[pi];
+    std::vector<Pending> sg;
+    greedy_groups(
+        pg, passes[pi].members, sg,
+        [&](const Pending &p, int i, uint64_t gmask, uint64_t, bool gdiag) {
+          const int width = popcount64(p.qmask | gmask);
+          if (p.all_diag && gdiag) return width <= D;
+          // a non-diagonal block may reach outside the tile only through
+          // qubits that are controls of every member: then they are
+          // detected as controls of the product
+          const uint64_t out = p.out_union | (gmask & ~T);
+          return width <= kin && (out & ~(p.cl_and & cl[i])) == 0;
+        },
+        [&](Pending &p, int i, uint64_t gmask) {
+          p.out_union |= gmask & ~T;
+          p.cl_and &= cl[i];
+        });
+    for (Pending &p : sg) {
+      subs.push_back(std::move(p));
+      sub_pass.push_back((int)pi);
+    }
+  }
+  std::vector<Block> done(subs.size());
+  std::vector<char> keep(subs.size(), 0);
+  parallel_for(subs.size(), [&](size_t i) { keep[i] = finish_block(pg, subs[i], false, done[i]) ? 1 : 0; });
+  (void)err;
+  size_t si = 0;
+  for (size_t pi = 0; pi < passes.size(); pi++) {
+    const uint64_t T = tmask[pi];
+    std::vector<Block> members;
+    for (; si < subs.size() && sub_pass[si] == (int)pi; si++)
+      if (keep[si]) members.push_back(std::move(done[si]));
+    bool ok = true;
+    for (const Block &b : members) {
+      if (b.kind == BK_DENSE) {
+        ok = ok && b.k <= 4;
+        for (int j = 0; j < b.k; j++) ok = ok && ((T >> b.q[j]) & 1);
+      } else if (b.kind != BK_DIAG) {
+        ok = false;
+      }
+    }
+    if (!ok) {  // cannot happen by construction; the members stay valid alone
+      for (Block &b : members) out.push_back(std::move(b));
+      continue;
+    }
+    // split at the shared-memory limits of one pass
+    size_t b0 = 0;
+    while (b0 < members.size()) {
+      size_t b1 = b0;
+      int pool = 0;
+      while (b1 < members.size() && (int)(b1 - b0) < kTileMaxOps) {
+        const Block &b = members[b1];
+        const int ent = b.kind == BK_DENSE ? (1 << (2 * b.k)) : (1 << b.k);
+        if (b1 > b0 && pool + ent > kTilePool) break;
+        pool += ent;
+        b1++;
+      }
+      if (b1 - b0 == 1) {
+        out.push_back(std::move(members[b0]));
+      } else {
+        Block t;
+        t.kind = BK_TILE;
+        t.k = m;
+        int w = 0;
+        for (int q = 0; q < 64; q++)
+          if ((T >> q) & 1) t.tile_q[w++] = q;
+        t.meta = 5;
+        t.n_gates = 0;
+        for (size_t j = b0; j < b1; j++) {
+          t.n_gates += members[j].n_gates;
+          t.sub.push_back(std::move(members[j]));
+        }
+        out.push_back(std::move(t));
+      }
+      b0 = b1;
+    }
+  }
+  return QS_OK;
+}
+
 }  // namespace
 
 void parallel_blocks(size_t n, const std::function<void(size_t)> &f) { parallel_for(n, f); }
+
+int tile_bits_of(const qs_opts &o, bool c128) {
+  if (o.tile_bits > 0) return std::min(o.tile_bits, c128 ? kMaxTileBits - 1 : kMaxTileBits);
+  return c128 ? 12 : 13;  // 64 KiB of amplitudes
+}
+
+int tile_k_of(const qs_opts &o) { return o.tile_k > 0 ? std::min(o.tile_k, 4) : 3; }
 
 void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_record &r) {
   std::memset(&r, 0, sizeof(r));
@@ -230,6 +438,9 @@ void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_recor
   r.nctrl = (uint8_t)b.nctrl;
   r.tc = b.tc ? 1 : 0;
   for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
+  if (b.kind == BK_TILE)
+    for (int j = 0; j < QS_MAX_DIAG; j++)
+      r.qubits[j] = kTileLowBits + j < b.k ? (int8_t)b.tile_q[kTileLowBits + j] : (int8_t)-1;
   r.meta = (uint8_t)b.meta;
   r.op = b.n_gates == 1 ? (uint8_t)b.first_op : (uint8_t)255;
   r.n_gates = b.n_gates;
@@ -247,7 +458,7 @@ double block_bytes(const Block &b, int n, int amp_bytes) {
 
 qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
                      const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
-                     PlanStats &stats, std::string &err) {
+                     PlanStats &stats, std::string &err, bool c128) {
   plan.clear();
   stats = PlanStats();
   stats.gates_in = (int)n_gates;
@@ -289,6 +500,17 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     return QS_EUNSUPPORTED;
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+  if (flags & QS_TILE) {
+    const int tmax = c128 ? kMaxTileBits - 1 : kMaxTileBits;
+    if (opts.tile_bits != 0 && (opts.tile_bits < 8 || opts.tile_bits > tmax)) {
+      err = "opts.tile_bits out of range";
+      return QS_EINVAL;
+    }
+    if (opts.tile_k < 0 || opts.tile_k > 4) {
+      err = "opts.tile_k out of range (0..4)";
+      return QS_EINVAL;
+    }
+  }
 
   // (0) rotation folding (an IR rewrite; exact)
   std::vector<qs_gate> folded;
@@ -367,6 +589,18 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
 
   // (2) grouping
   std::vector<Pending> groups;
+  std::vector<int> all(pg.size());
+  for (size_t i = 0; i < pg.size(); i++) all[i] = (int)i;
+  const bool tiled = (flags & QS_TILE) && n > tile_bits_of(opts, c128);
+  if (tiled) {
+    std::vector<Block> tplan;
+    qs_status ts = tile_plan(n, pg, all, opts, c128, tplan, err);
+    if (ts != QS_OK) return ts;
+    plan.reserve(tplan.size() + reloc.size());
+    push_exchanges(reloc, plan);
+    for (Block &b : tplan) plan.push_back(std::move(b));
+    return QS_OK;
+  }
   if (!fuse && !dfuse) {
     groups.resize(pg.size());
     for (size_t i = 0; i < pg.size(); i++) {
@@ -375,45 +609,12 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
       groups[i].all_diag = op_info(pg[i].op).diagonal;
     }
   } else {
-    // Greedy placement with commutation: a gate may join any group at or
-    // after the last group it cannot commute past. Two gates commute when
-    // both act diagonally on every qubit they share.
-    std::vector<int> last_any(64, -1), last_nd(64, -1);
-    for (size_t i = 0; i < pg.size(); i++) {
-      const qs_gate &g = pg[i];
-      const bool gdiag = op_info(g.op).diagonal;
-      uint64_t gmask = 0;
-      int lower = -1;
-      for (int j = 0; j < g.nq; j++) {
-        int q = g.q[j];
-        gmask |= 1ull << q;
-        lower = std::max(lower, gate_diag_on(g, j) ? last_nd[q] : last_any[q]);
-      }
-      int chosen = -1;
-      for (int b = std::max(lower, 0); b < (int)groups.size(); b++) {
-        const Pending &p = groups[b];
-        int width = popcount64(p.qmask | gmask);
-        bool nd = p.all_diag && gdiag;
-        int limit = nd ? (dfuse ? D : std::max(K, 1)) : K;
-        if (width <= limit) {
-          chosen = b;
-          break;
-        }
-      }
-      if (chosen < 0) {
-        groups.emplace_back();
-        chosen = (int)groups.size() - 1;
-      }
-      Pending &p = groups[chosen];
-      p.members.push_back((int)i);
-      p.qmask |= gmask;
-      p.all_diag = p.all_diag && gdiag;
-      for (int j = 0; j < g.nq; j++) {
-        int q = g.q[j];
-        last_any[q] = std::max(last_any[q], chosen);
-        if (!gate_diag_on(g, j)) last_nd[q] = std::max(last_nd[q], chosen);
-      }
-    }
+    greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
+      const int width = popcount64(p.qmask | gmask);
+      const bool nd = p.all_diag && gdiag;
+      const int limit = nd ? (dfuse ? D : std::max(K, 1)) : K;
+      return width <= limit;
+    });
   }
 
   // (3) products and classification
@@ -423,16 +624,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i]) ? 1 : 0;
   });
   plan.reserve(groups.size() + reloc.size());
-  for (auto &pr : reloc) {  // the exchanges run first
-    Block b;
-    b.kind = BK_PERMUTE;
-    b.k = 2;
-    b.q[0] = std::min(pr.first, pr.second);
-    b.q[1] = std::max(pr.first, pr.second);
-    b.n_gates = 0;
-    b.meta = 3;
-    plan.push_back(std::move(b));
-  }
+  push_exchanges(reloc, plan);
   for (size_t i = 0; i < groups.size(); i++)
     if (keep[i]) plan.push_back(std::move(done[i]));
   const bool tf32 = opts.tc_precision == 1;

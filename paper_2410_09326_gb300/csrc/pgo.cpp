@@ -179,7 +179,7 @@ qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t 
   for (size_t c = 0; c < cands.size(); c++) {
     int8_t perm[QS_MAX_QUBITS];
     for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
-    qs_status s = build_plan(n, gates, n_gates, cands[c], o, perm, plan, stats, err);
+    qs_status s = build_plan(n, gates, n_gates, cands[c], o, perm, plan, stats, err, c128);
     if (s != QS_OK) return s;
     first[c] = feats.size() / QS_MLP_FEATURES;
     for (size_t i = 0; i < plan.size(); i++) {
@@ -228,7 +228,7 @@ qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates
   for (uint64_t f : cands) {
     int8_t perm[QS_MAX_QUBITS];
     for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
-    qs_status s = build_plan(n, gates, n_gates, f, o, perm, plan, stats, err);
+    qs_status s = build_plan(n, gates, n_gates, f, o, perm, plan, stats, err, c128);
     if (s != QS_OK) return s;
     const double ms = predict_plan_ms(plan, n, c128 ? 16 : 8, t, peak);
     if (ms < best * 0.999) {

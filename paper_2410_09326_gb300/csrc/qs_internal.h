@@ -41,9 +41,11 @@ bool gate_diag_on(const qs_gate &g, int j);
 // ---------------------------------------------------------------------------
 // Plan: the list of kernels one qs_apply_circuit call launches
 // ---------------------------------------------------------------------------
-enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2 };
+enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2, BK_TILE = 3 };
 
 constexpr int kMaxFixed = 24;  // targets + controls handled by the index insert
+constexpr int kMaxTileBits = 14;  // widest shared-memory tile (QS_TILE)
+constexpr int kTileLowBits = 4;   // contiguous low bits every tile includes (128-byte c64 runs)
 
 struct Block {
   BlockKind kind = BK_DENSE;
@@ -58,6 +60,11 @@ struct Block {
   bool tc = false;
   bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
+  // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
+  // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,
+  // dense targets inside the tile, diagonal qubits and controls anywhere
+  int tile_q[kMaxTileBits] = {0};
+  std::vector<Block> sub;
 };
 
 struct PlanStats {
@@ -70,9 +77,14 @@ struct PlanStats {
 // Virtual swap + fusion + classification. Gates are logical; perm is the
 // state's logical->physical map, updated in place for absorbed SWAPs.
 // Returns QS_OK or QS_EINVAL (message in err).
+// c128 selects the amplitude size the default tile width is computed for.
 qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
                      const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
-                     PlanStats &stats, std::string &err);
+                     PlanStats &stats, std::string &err, bool c128 = false);
+
+// Tile width QS_TILE uses for these options and amplitude type.
+int tile_bits_of(const qs_opts &o, bool c128);
+int tile_k_of(const qs_opts &o);
 
 double block_bytes(const Block &b, int n, int amp_bytes);
 

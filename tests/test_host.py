@@ -109,13 +109,15 @@ def apply_block(psi, n, rec, mat):
     return out
 
 
-def plan_state(n, gates, flags, init=None):
-    recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), flags)
+def plan_state(n, gates, flags, init=None, opts=None):
+    recs, mats, perm = qs.qs_plan(n, qs.gates_to_array(gates), flags, opts=opts)
     psi = np.zeros(1 << n, dtype=complex)
     psi[0] = 1
     if init is not None:
         psi = init.copy()
     for r, m in zip(recs, mats):
+        if r.kind == 3:
+            continue  # a tile pass: its member blocks follow
         psi = apply_block(psi, n, r, m)
     return psi, perm, recs
 
@@ -322,3 +324,82 @@ def test_relocation_leaves_balanced_circuits_alone():
     n, gates = cg.config0_circuit(0)
     recs, _, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_RELOCATE)
     assert not any(r.kind == 2 and r.n_gates == 0 for r in recs)
+
+
+def tile_opts(bits, k=0):
+    o = qs.qs_default_opts()
+    o.tile_bits = bits
+    o.tile_k = k
+    return o
+
+
+def tile_groups(recs):
+    """(tile record, [member records]) for every tile pass of a plan."""
+    out = []
+    for r in recs:
+        if r.kind == 3:
+            out.append((r, []))
+        elif out and r.index == out[-1][0].index:
+            out[-1][1].append(r)
+    return out
+
+
+@pytest.mark.parametrize("bits,k", [(8, 1), (8, 2), (8, 3), (9, 4), (11, 3)])
+def test_tile_plan_reproduces_oracle(bits, k):
+    """Cache-blocked passes: applying every pass's member blocks in order (the
+    work one tile pass does per tile) gives the oracle's state; dense members
+    only touch the tile's qubits, and each pass has at least two members."""
+    o = tile_opts(bits, k)
+    cases = [(12, cg.all_gate_types_circuit(12, 300, cg.SplitMix64(77 + bits + k))),
+             (13, cg.random_layered(13, 6, cg.SplitMix64(78 + k), n_swaps=6)),
+             (12, cg.qft(12, x=1234)[0])]
+    for n, gates in cases:
+        want, operm = oracle.simulate(cg.to_qasm(n, gates))
+        got, perm, recs = plan_state(n, gates, qs.QS_VSWAP | qs.QS_TILE, opts=o)
+        assert list(perm) == list(operm)
+        assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+        groups = tile_groups(recs)
+        assert groups
+        for t, members in groups:
+            assert t.k == bits and t.meta == 5 and len(members) >= 2
+            tile = set(range(4)) | {int(q) for q in t.qubits if q >= 0}
+            assert len(tile) == min(bits, 4 + 10)
+            assert t.n_gates == sum(m.n_gates for m in members)
+            for m in members:
+                if m.kind == 0:
+                    # one gate alone may be wider than tile_k (a CX at tile_k = 1)
+                    assert m.k <= max(k, 2) and {int(m.qubits[j]) for j in range(m.k)} <= tile
+                else:
+                    assert m.kind == 1
+
+
+def test_tile_plan_options_and_small_states():
+    arr = qs.gates_to_array(cg.random_layered(12, 3, cg.SplitMix64(5)))
+    for bad in (tile_opts(7), tile_opts(15), tile_opts(9, 5)):
+        with pytest.raises(qs.QsError):
+            qs.qs_plan(12, arr, qs.QS_TILE, opts=bad)
+    # a state no wider than one tile runs without tile passes
+    recs, _, _ = qs.qs_plan(12, arr, qs.QS_TILE, opts=tile_opts(12))
+    assert not any(r.kind == 3 for r in recs)
+    recs, _, _ = qs.qs_plan(12, arr, qs.QS_TILE, opts=tile_opts(11))
+    assert any(r.kind == 3 for r in recs)
+
+
+def test_tile_passes_cut_hbm_passes_at_n30():
+    """At the benchmark width the tile planner needs far fewer passes over
+    the state than 5-qubit fusion (the point of cache blocking)."""
+    c = cg.config1_circuits(n=30)
+    fused = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG
+    for name in ("ghz", "qft", "random"):
+        arr = qs.gates_to_array(c[name][1])
+        top_fused = [r for r in qs.qs_plan(30, arr, fused)[0]]
+        top_tiled = [r for r in qs.qs_plan(30, arr, qs.QS_VSWAP | qs.QS_TILE)[0] if not tile_member(r)]
+        assert len(top_tiled) < 0.5 * len(top_fused), (name, len(top_tiled), len(top_fused))
+
+
+def tile_member(r, _last=[None]):
+    # records after a tile record that carry its index are its members
+    if r.kind == 3:
+        _last[0] = r.index
+        return False
+    return r.index == _last[0]
