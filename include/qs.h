@@ -86,7 +86,7 @@ typedef struct {
 #define QS_PLAIN ((uint64_t)0)              /* one kernel per gate, SWAP moves data */
 #define QS_VSWAP ((uint64_t)1 << 0)         /* SWAPs become relabellings of perm */
 #define QS_FUSE ((uint64_t)1 << 1)          /* k-qubit fusion, k from QS_FUSE_K */
-#define QS_DIAG ((uint64_t)1 << 2)          /* diagonal runs fuse up to QS_MAX_DIAG wide */
+#define QS_DIAG ((uint64_t)1 << 2)          /* diagonal runs fuse, any width */
 #define QS_TC ((uint64_t)1 << 3)            /* dense k>=4 blocks on tensor cores (opts->tc_precision) */
 #define QS_PROFILE ((uint64_t)1 << 4)       /* time every block with CUDA events */
 #define QS_RELOCATE ((uint64_t)1 << 5)      /* profile-guided hot-qubit relocation */
@@ -105,7 +105,7 @@ typedef struct {
   double t_ratio;       /* rotation-folding activation: T count / gates (paper: e.g. 10%) */
   int low_bits;         /* physical bits below this are "fast" (chunk-segment analogue) */
   double reloc_share;   /* relocate a high qubit carrying >= this share of block time */
-  int diag_max;         /* widest diagonal block, 1..QS_MAX_DIAG */
+  int diag_max;         /* widest diagonal phase table, 1..QS_MAX_DIAG (wider runs: polynomials) */
   int threads;          /* launch override: threads per CTA (0 = tuned default) */
   double peak_gbs;      /* HBM copy bandwidth the cost model scales its priors by */
   int tc_precision;     /* QS_TC operands: 0 = two FP16 halves (k = 4..6), 1 = 3 x TF32 (k = 4, 5) */
@@ -160,8 +160,9 @@ qs_status qs_parse_qasm(const char *text, int *n_qubits, qs_gate *gates, size_t 
  * one kernel per gate; QS_VSWAP absorbs SWAPs into perm (Sec. III-D "Virtual
  * swap"); QS_FUSE | QS_FUSE_K(k) groups gates into dense blocks of at most k
  * qubits, commuting gates past each other only where they act diagonally on
- * every shared qubit; QS_DIAG lets diagonal runs grow to opts->diag_max
- * qubits; QS_TC runs dense blocks with 4..6 targets on the tensor cores;
+ * every shared qubit; QS_DIAG lets diagonal runs grow: up to opts->diag_max
+ * qubits as a phase table, wider (any width, states of more than 10 qubits)
+ * as a phase polynomial exp(i(c + sum a_j x_j + sum b_jl x_j x_l)); QS_TC runs dense blocks with 4..6 targets on the tensor cores;
  * QS_TILE groups gates (same commutation rule) into passes whose non-diagonal
  * qubits fit a tile of opts->tile_bits qubits and applies each pass -- its
  * gates fused again, at most opts->tile_k wide -- in shared memory during one
@@ -186,7 +187,8 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
 typedef struct {
   int32_t index;     /* launch order within the last apply call */
   uint8_t kind;      /* 0 dense block, 1 diagonal block, 2 physical bit exchange,
-                        3 tile pass (QS_TILE: several blocks in one HBM pass) */
+                        3 tile pass (QS_TILE: several blocks in one HBM pass),
+                        4 phase polynomial (a diagonal run wider than opts->diag_max) */
   uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) /
                         tile qubits (tile pass) */
   uint8_t nctrl;     /* control bits that must be 1: only 2^(n-nctrl) amplitudes move */
@@ -265,7 +267,9 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
  * as interleaved (re, im) pairs, block after block: (2^k)^2 entries for a
  * dense block (row-major over the block's ascending physical qubits, local
  * index sum_j bit(q_j) << j), 2^k phases for a diagonal block, none for an
- * exchange or a tile pass. A tile pass's record is followed by the records
+ * exchange or a tile pass; for a phase polynomial (kind 4) its k qubits as
+ * (physical qubit, linear angle) pairs, then (constant angle, 0), then
+ * (pair angle, 0) for every qubit pair j < l in row order. A tile pass's record is followed by the records
  * (and matrices) of its member blocks in the order the pass applies them;
  * they carry the pass's index. *n_blocks (records) and *mats_len (complex
  * entries) receive the totals.

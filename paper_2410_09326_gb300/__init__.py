@@ -353,7 +353,9 @@ def qs_device_ptr(st):
 
 def qs_plan(n, gates, flags=QS_PLAIN, opts=None, perm=None):
     """Host passes only. Returns (records, matrices, perm): matrices[i] is the
-    block's complex128 matrix ((2^k, 2^k) dense, (2^k,) diagonal, None exchange)."""
+    block's complex128 matrix ((2^k, 2^k) dense, (2^k,) diagonal, None exchange
+    or tile pass) or, for a phase polynomial, a dict of its qubits, linear
+    angles a, constant c and pair angles b (upper triangle)."""
     lib = load()
     gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
     pm = (ctypes.c_int8 * n)(*(range(n) if perm is None else [int(x) for x in perm]))
@@ -380,6 +382,15 @@ def qs_plan(n, gates, flags=QS_PLAIN, opts=None, perm=None):
             d = 1 << r.k
             out.append(cm[off: off + d].copy())
             off += d
+        elif r.kind == 4:
+            k = r.k
+            qa = cm[off: off + k]
+            c = cm[off + k].real
+            b = np.zeros((k, k))
+            iu = np.triu_indices(k, 1)
+            b[iu] = cm[off + k + 1: off + k + 1 + len(iu[0])].real
+            out.append({"qubits": qa.real.astype(np.int64), "a": qa.imag.copy(), "c": c, "b": b})
+            off += k + 1 + len(iu[0])
         else:
             out.append(None)
     return list(recs)[: nb.value], out, np.array(list(pm), dtype=np.int64)

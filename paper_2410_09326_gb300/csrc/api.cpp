@@ -526,15 +526,21 @@ qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, c
   if (s != QS_OK) return fail(s, "qs_plan: " + err);
   std::memcpy(perm_inout, perm, n);
   size_t mlen = 0, nr = 0;
+  auto put = [&](double re, double im) {
+    if (mats && mlen < mats_cap) {
+      mats[2 * mlen] = re;
+      mats[2 * mlen + 1] = im;
+    }
+    mlen++;
+  };
   auto emit = [&](const Block &b, int index) {
     if (recs && nr < cap) fill_record(b, index, n, 8, recs[nr]);
     nr++;
-    for (const cd &z : b.mat) {
-      if (mats && mlen < mats_cap) {
-        mats[2 * mlen] = z.real();
-        mats[2 * mlen + 1] = z.imag();
-      }
-      mlen++;
+    for (const cd &z : b.mat) put(z.real(), z.imag());
+    if (b.kind == BK_PHASE) {
+      for (int j = 0; j < b.k; j++) put((double)b.ph_q[j], b.ph_a[j]);
+      put(b.ph_c, 0.0);
+      for (double x : b.ph_b) put(x, 0.0);
     }
   };
   for (size_t i = 0; i < plan.size(); i++) {

@@ -219,7 +219,7 @@ qs_status upload_plan(qs_batch *bt, uint64_t flags) {
     int8_t perm[QS_MAX_QUBITS];
     for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
     qs_status s = build_plan(n, bt->gates[c].data(), bt->gates[c].size(), flags & ~(uint64_t)(QS_TC | QS_TILE), bt->opts,
-                             perm, plan, stats, err);
+                             perm, plan, stats, err, false, /*allow_phase=*/false);
     if (s != QS_OK) return bfail(s, "qs_batch: circuit " + std::to_string(c) + ": " + err);
     bt->final_perm[c].assign(perm, perm + n);
     circs[c].amps = (float2 *)state_amps(bt->states[c]);

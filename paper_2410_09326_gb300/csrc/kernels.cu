@@ -320,7 +320,7 @@ const DevInfo &dev_info() {
 }
 
 bool block_needs_dev_matrix(const Block &b, bool c128) {
-  if (b.kind == BK_TILE) return true;
+  if (b.kind == BK_TILE || b.kind == BK_PHASE) return true;
   if (b.kind != BK_DENSE) return false;
   if (b.tc && !c128) return true;
   return b.k == 6 || (c128 && b.k == 5);
@@ -329,6 +329,7 @@ bool block_needs_dev_matrix(const Block &b, bool c128) {
 size_t block_dev_matrix_bytes(const Block &b, bool c128) {
   if (!block_needs_dev_matrix(b, c128)) return 0;
   if (b.kind == BK_TILE) return tile_desc_bytes(b, c128);
+  if (b.kind == BK_PHASE) return phase_desc_bytes(b, c128);
   if (b.tc && !c128) return b.tc_tf32 ? tc_b_floats(b.k) * sizeof(float) : tc16_b_bytes(b.k);
   return b.mat.size() * (c128 ? 16 : 8);
 }
@@ -336,6 +337,10 @@ size_t block_dev_matrix_bytes(const Block &b, bool c128) {
 void fill_dev_matrix(const Block &b, bool c128, void *host_out) {
   if (b.kind == BK_TILE) {
     tile_fill_desc(b, c128, host_out);
+    return;
+  }
+  if (b.kind == BK_PHASE) {
+    phase_fill_desc(b, c128, host_out);
     return;
   }
   if (b.tc && !c128) {
@@ -358,6 +363,7 @@ cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &
                                      int *err, cudaStream_t s, int threads) {
   if (threads <= 0) threads = 256;
   if (b.kind == BK_TILE) return run_tile(amps, n, c128, b, dev_mat, s);
+  if (b.kind == BK_PHASE) return run_phase(amps, n, c128, b, dev_mat, s);
   if (b.kind == BK_DENSE && b.tc && !c128)
     return b.tc_tf32 ? run_dense_tc((float2 *)amps, n, b, dev_mat, err, s)
                      : run_dense_tc16((float2 *)amps, n, b, dev_mat, err, s);
@@ -553,6 +559,7 @@ __global__ void __launch_bounds__(256) k_distance(const Ta *__restrict__ a, cons
 
 template <typename T> size_t param_bytes_t(const Block &b) {
   if (b.kind == BK_TILE) return 2 * sizeof(T *) + sizeof(long long) + tile_desc_bytes(b, sizeof(T) == 16);
+  if (b.kind == BK_PHASE) return 2 * sizeof(T *) + sizeof(long long) + phase_desc_bytes(b, sizeof(T) == 16);
   if (b.kind == BK_PERMUTE) return sizeof(T *) + sizeof(long long) + 2 * sizeof(int);
   if (b.kind == BK_DIAG) return sizeof(T *) + sizeof(DiagParam<T>);
   switch (b.k) {

@@ -218,6 +218,12 @@ size_t tile_smem_bytes(const Block &b, bool c128);
 void tile_fill_desc(const Block &b, bool c128, void *out);
 cudaError_t run_tile(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s);
 
+// Phase-polynomial diagonal blocks (phase.cu), n > 10: factor table and
+// chunk terms in device memory.
+size_t phase_desc_bytes(const Block &b, bool c128);
+void phase_fill_desc(const Block &b, bool c128, void *out);
+cudaError_t run_phase(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s);
+
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 cudaError_t run_dense_c128(double2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 

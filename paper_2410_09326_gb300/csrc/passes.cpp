@@ -165,7 +165,68 @@ uint64_t ctrl_like_mask(const qs_gate &g) {
 
 // Turns a group of gates into a classified Block (dense/diag/permute);
 // returns false when the product is the identity (nothing to launch).
-bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_permute, Block &out) {
+double wrap_angle(double a) {
+  a = std::remainder(a, 2 * M_PI);  // [-pi, pi]
+  return a <= -M_PI ? a + 2 * M_PI : a;
+}
+
+// Phase polynomial of a run of diagonal gates (each on at most two qubits):
+// gate g contributes arg g(00) + (arg g(10) - arg g(00)) x_0 +
+// (arg g(01) - arg g(00)) x_1 + (arg g(11) - arg g(10) - arg g(01) +
+// arg g(00)) x_0 x_1, which equals arg g(x) on all four inputs. Returns false
+// when the product is the identity.
+bool phase_block(const std::vector<qs_gate> &pg, const Pending &p, const int *qs, int w, Block &out) {
+  std::vector<double> a(w, 0.0), b((size_t)w * (w - 1) / 2, 0.0);
+  double c = 0;
+  std::vector<cd> G;
+  for (int gi : p.members) {
+    const qs_gate &g = pg[gi];
+    gate_full_matrix(g, G);
+    const int d = 1 << g.nq;
+    double ph[4] = {0, 0, 0, 0};
+    for (int l = 0; l < d; l++) ph[l] = std::arg(G[(size_t)l * d + l]);
+    const int j0 = pos_of(qs, w, g.q[0]);
+    c += ph[0];
+    a[j0] += ph[1] - ph[0];
+    if (g.nq == 2) {
+      const int j1 = pos_of(qs, w, g.q[1]);
+      a[j1] += ph[2] - ph[0];
+      const double x = ph[3] - ph[1] - ph[2] + ph[0];
+      b[j0 < j1 ? tri_index(j0, j1, w) : tri_index(j1, j0, w)] += x;
+    }
+  }
+  // keep the qubits that still carry a term
+  auto zero = [](double v) { return std::fabs(wrap_angle(v)) <= kEps; };
+  std::vector<char> used(w, 0);
+  for (int j = 0; j < w; j++) {
+    if (!zero(a[j])) used[j] = 1;
+    for (int l = j + 1; l < w; l++)
+      if (!zero(b[tri_index(j, l, w)])) used[j] = used[l] = 1;
+  }
+  std::vector<int> keep;
+  for (int j = 0; j < w; j++)
+    if (used[j]) keep.push_back(j);
+  const int k = (int)keep.size();
+  if (k == 0 && zero(c)) return false;
+  out.kind = BK_PHASE;
+  out.k = k;
+  out.ph_c = wrap_angle(c);
+  out.ph_q.resize(k);
+  out.ph_a.resize(k);
+  out.ph_b.assign(k > 1 ? (size_t)k * (k - 1) / 2 : 0, 0.0);
+  for (int j = 0; j < k; j++) {
+    out.ph_q[j] = qs[keep[j]];
+    out.ph_a[j] = wrap_angle(a[keep[j]]);
+    for (int l = j + 1; l < k; l++) out.ph_b[tri_index(j, l, k)] = wrap_angle(b[tri_index(keep[j], keep[l], w)]);
+  }
+  for (int j = 0; j < std::min(k, QS_MAX_DIAG); j++) out.q[j] = out.ph_q[j];
+  return true;
+}
+
+// table_max: widest diagonal run kept as a phase table; wider all-diagonal
+// groups become phase polynomials when phase_ok.
+bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_permute, Block &out,
+                  int table_max = QS_MAX_DIAG, bool phase_ok = false) {
   int qs[64], w = 0;
   for (int q = 0; q < 64; q++)
     if ((p.qmask >> q) & 1) qs[w++] = q;
@@ -184,6 +245,14 @@ bool finish_block(const std::vector<qs_gate> &pg, const Pending &p, bool allow_p
     return true;
   }
   std::vector<cd> G;
+  if (p.all_diag && phase_ok && w > table_max) {
+    const int first_op = out.first_op, meta = out.meta, ng = out.n_gates;
+    if (!phase_block(pg, p, qs, w, out)) return false;
+    out.first_op = first_op;
+    out.meta = meta;
+    out.n_gates = ng;
+    return true;
+  }
   if (p.all_diag) {
     // diagonal table over the w qubits: product of every member's diagonal
     std::vector<cd> tab((size_t)1 << w, cd(1, 0));
@@ -458,7 +527,7 @@ double block_bytes(const Block &b, int n, int amp_bytes) {
 
 qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
                      const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
-                     PlanStats &stats, std::string &err, bool c128) {
+                     PlanStats &stats, std::string &err, bool c128, bool allow_phase) {
   plan.clear();
   stats = PlanStats();
   stats.gates_in = (int)n_gates;
@@ -609,10 +678,14 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
       groups[i].all_diag = op_info(pg[i].op).diagonal;
     }
   } else {
+    // diagonal runs: up to D qubits as a phase table, any width as a phase
+    // polynomial (states of at least 11 qubits, which the kernel needs)
+    const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
+    const int dlimit = phase_ok ? 64 : D;
     greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
       const int width = popcount64(p.qmask | gmask);
       const bool nd = p.all_diag && gdiag;
-      const int limit = nd ? (dfuse ? D : std::max(K, 1)) : K;
+      const int limit = nd ? (dfuse ? dlimit : std::max(K, 1)) : K;
       return width <= limit;
     });
   }
@@ -620,8 +693,9 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   // (3) products and classification
   std::vector<Block> done(groups.size());
   std::vector<char> keep(groups.size(), 0);
+  const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
   parallel_for(groups.size(), [&](size_t i) {
-    if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i]) ? 1 : 0;
+    if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i], D, phase_ok) ? 1 : 0;
   });
   plan.reserve(groups.size() + reloc.size());
   push_exchanges(reloc, plan);

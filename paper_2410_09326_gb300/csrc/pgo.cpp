@@ -21,6 +21,9 @@
 namespace qs {
 
 int block_class(const Block &b) {
+  // phase polynomials share the diagonal kind with the "low" bit set, which
+  // only dense classes use otherwise
+  if (b.kind == BK_PHASE) return 64 + 8 * BK_DIAG + 7;
   // "low": bits 0 and 1 are both targets, so a thread's group is a run of
   // >= 4 contiguous amplitudes and a warp's accesses are strided
   int low = 0;
@@ -128,7 +131,7 @@ void record_features(const qs_block_record &r, int n, bool c128, float *f) {
   f[1] = k / 6.f;
   f[2] = r.nctrl / 8.f;
   f[3] = r.kind == BK_DENSE;
-  f[4] = r.kind == BK_DIAG;
+  f[4] = r.kind == BK_DIAG || r.kind == BK_PHASE;
   f[5] = r.kind == BK_PERMUTE;
   f[6] = r.tc ? 1.f : 0.f;
   f[7] = (r.kind == BK_DENSE && bit[0] && bit[1]) ? 1.f : 0.f;

@@ -41,7 +41,7 @@ bool gate_diag_on(const qs_gate &g, int j);
 // ---------------------------------------------------------------------------
 // Plan: the list of kernels one qs_apply_circuit call launches
 // ---------------------------------------------------------------------------
-enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2, BK_TILE = 3 };
+enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2, BK_TILE = 3, BK_PHASE = 4 };
 
 constexpr int kMaxFixed = 24;  // targets + controls handled by the index insert
 constexpr int kMaxTileBits = 14;  // widest shared-memory tile (QS_TILE)
@@ -65,7 +65,16 @@ struct Block {
   // dense targets inside the tile, diagonal qubits and controls anywhere
   int tile_q[kMaxTileBits] = {0};
   std::vector<Block> sub;
+  // phase polynomial (BK_PHASE): the block multiplies amplitude x by
+  // exp(i (ph_c + sum_j ph_a[j] x_{ph_q[j]} + sum_{j<l} ph_b[j,l] x_{ph_q[j]} x_{ph_q[l]})),
+  // k = ph_q.size(), ph_b upper triangle in row order, angles in (-pi, pi]
+  std::vector<int> ph_q;
+  std::vector<double> ph_a, ph_b;
+  double ph_c = 0;
 };
+
+// Index of the pair (j, l), j < l < w, in a row-order upper triangle.
+inline size_t tri_index(int j, int l, int w) { return (size_t)j * (2 * w - j - 1) / 2 + (l - j - 1); }
 
 struct PlanStats {
   int gates_in = 0;
@@ -80,7 +89,7 @@ struct PlanStats {
 // c128 selects the amplitude size the default tile width is computed for.
 qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags,
                      const qs_opts &opts, int8_t *perm, std::vector<Block> &plan,
-                     PlanStats &stats, std::string &err, bool c128 = false);
+                     PlanStats &stats, std::string &err, bool c128 = false, bool allow_phase = true);
 
 // Tile width QS_TILE uses for these options and amplitude type.
 int tile_bits_of(const qs_opts &o, bool c128);

@@ -89,6 +89,15 @@ def apply_block(psi, n, rec, mat):
         a, b = rec.qubits[0], rec.qubits[1]
         flip = ((idx >> a) & 1) ^ ((idx >> b) & 1)
         return psi[idx ^ (flip << a) ^ (flip << b)]
+    if rec.kind == 4:  # phase polynomial
+        q = mat["qubits"]
+        bits = [((idx >> int(x)) & 1).astype(float) for x in q]
+        ang = np.full(1 << n, mat["c"])
+        for j in range(len(q)):
+            ang += mat["a"][j] * bits[j]
+            for l in range(j + 1, len(q)):
+                ang += mat["b"][j, l] * bits[j] * bits[l]
+        return psi * np.exp(1j * ang)
     qubits = [int(rec.qubits[j]) for j in range(rec.k)]
     cm = int(rec.cmask)
     on = (idx & cm) == cm
@@ -387,10 +396,11 @@ def test_tile_plan_options_and_small_states():
 
 def test_tile_passes_cut_hbm_passes_at_n30():
     """At the benchmark width the tile planner needs far fewer passes over
-    the state than 5-qubit fusion (the point of cache blocking)."""
+    the state than 5-qubit fusion (the point of cache blocking) on circuits
+    of dense gates."""
     c = cg.config1_circuits(n=30)
     fused = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG
-    for name in ("ghz", "qft", "random"):
+    for name in ("ghz", "random"):
         arr = qs.gates_to_array(c[name][1])
         top_fused = [r for r in qs.qs_plan(30, arr, fused)[0]]
         top_tiled = [r for r in qs.qs_plan(30, arr, qs.QS_VSWAP | qs.QS_TILE)[0] if not tile_member(r)]
@@ -403,3 +413,44 @@ def tile_member(r, _last=[None]):
         _last[0] = r.index
         return False
     return r.index == _last[0]
+
+
+def diagonal_circuit(n, count, seed, dense_every=0):
+    """Random diagonal gates of every kind (optionally with an H now and then)."""
+    rng = cg.SplitMix64(seed)
+    names = [("t", 1, 0), ("s", 1, 0), ("z", 1, 0), ("sdg", 1, 0), ("tdg", 1, 0), ("rz", 1, 1), ("u1", 1, 1),
+             ("cp", 2, 1), ("cu1", 2, 1), ("cz", 2, 0), ("crz", 2, 1), ("rzz", 2, 1), ("id", 1, 0)]
+    gates = []
+    for i in range(count):
+        if dense_every and i % dense_every == dense_every - 1:
+            gates.append(("h", [rng.randint(n)], []))
+            continue
+        name, nq, npar = names[rng.randint(len(names))]
+        qs_ = rng.shuffle(list(range(n)))[:nq]
+        gates.append((name, qs_, [rng.uniform(-2 * math.pi, 2 * math.pi) for _ in range(npar)]))
+    return gates
+
+
+@pytest.mark.parametrize("n,seed,dense_every", [(11, 1, 0), (12, 2, 0), (13, 3, 25), (14, 4, 40)])
+def test_phase_polynomial_blocks_reproduce_oracle(n, seed, dense_every):
+    """Diagonal runs wider than the phase table become one phase polynomial
+    (kind 4): applying its constant, linear and pair angles gives the
+    oracle's state in FP64."""
+    gates = diagonal_circuit(n, 400, 600 + seed, dense_every)
+    want, _ = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, recs = plan_state(n, gates, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_DIAG)
+    assert any(r.kind == 4 and r.k > 10 for r in recs)
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+
+
+def test_qft_diagonal_ladders_become_polynomials():
+    n = 14
+    gates, x = cg.qft(n, x=4321)
+    want, _ = oracle.simulate(cg.to_qasm(n, gates))
+    got, perm, recs = plan_state(n, gates, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG)
+    assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
+    narrow = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG)[0]
+    assert any(r.kind == 4 for r in narrow)
+    # states of at most 10 qubits keep phase tables
+    recs10 = qs.qs_plan(10, qs.gates_to_array(cg.qft(10, x=5)[0]), qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG)[0]
+    assert not any(r.kind == 4 for r in recs10)
