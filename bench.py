@@ -158,6 +158,10 @@ def kernel_name(rec):
         return "k_permute"
     if rec.kind == 1:
         return "k_diag"
+    if rec.kind == 3:
+        return "k_tile"
+    if rec.kind == 4:
+        return "k_phase"
     return f"k_dense_k{rec.k}" + ("_tc" if rec.tc else "")
 
 
@@ -261,7 +265,8 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64 (f32 fused products, f64 reductions)", "data": "synthetic (seeded circuits)",
         "config": {"workload": "n=30 c64: GHZ + QFT(basis state, swap network) + 30-layer random (5% SWAP), "
-                               "PGO rules -> vswap + k<=5 fusion (tensor cores for k=4,5) + diagonal runs; "
+                               "PGO rules -> vswap + k<=5 fusion (tensor cores for k=4,5) + diagonal runs "
+                               "(tables <= 10 qubits, wider as phase polynomials); "
                                "FP64 probs of 16 qubits",
                    "n_qubits": n, "circuits": [c[0] for c in circuits],
                    "gates": [qs.qs_parse_qasm(t)[1].size for _, t in circuits],
@@ -369,7 +374,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-CASES = ("tc6", "tc5", "tc4", "dense3", "diag10", "permute", "probs")
+CASES = ("tc6", "tc5", "tc4", "dense3", "diag10", "phase", "tile", "permute", "probs")
 
 
 def run_case(args):
@@ -383,6 +388,7 @@ def run_case(args):
     k = {"tc6": 6, "tc5": 5, "tc4": 4, "dense3": 3}.get(args.case, 0)
     opts = qs.qs_default_opts()
     opts.tc_precision = args.tc_precision
+    opts.tc_row_threads = args.tc_rows
     if k:
         qubits = [1, 6, 11, 16, 21, 24][:k] if n > 24 else list(range(0, 2 * k, 2))
         if args.targets:
@@ -394,6 +400,16 @@ def run_case(args):
         qs_ = list(range(n - 10, n))
         gates = [("cp", [a, b], [rng.uniform(0, 3)]) for a, b in zip(qs_[:-1], qs_[1:])] + [("rz", [q], [0.3]) for q in qs_]
         flags = qs.QS_DIAG
+    elif args.case == "phase":
+        # a controlled-phase ladder over every qubit plus RZ on each: one
+        # phase polynomial spanning the whole register
+        gates = [("cp", [q, q + 1], [rng.uniform(0, 3)]) for q in range(n - 1)] + \
+                [("cp", [0, q], [rng.uniform(0, 3)]) for q in range(2, n)] + [("rz", [q], [0.3]) for q in range(n)]
+        flags = qs.QS_DIAG
+    elif args.case == "tile":
+        # four layers of the random circuit: tile passes of 13 qubits
+        gates = [g for g in cg.random_layered(n, 4, rng) if g[0] != "swap"]
+        flags = qs.QS_TILE
     elif args.case == "permute":
         gates = [("swap", [3, n - 2])]
         flags = qs.QS_PLAIN
@@ -402,13 +418,14 @@ def run_case(args):
         flags = qs.QS_PLAIN
     st = qs.qs_alloc_state(n, qs.QS_C64)
     arr = qs.gates_to_array(gates)
+    recs = []
     for _ in range(args.launches):
         if args.case == "probs":
             qs.qs_measure_probs(st, list(range(10)))
         else:
             qs.qs_apply_circuit(st, arr, flags | qs.QS_PROFILE, opts)
+            recs += qs.qs_profile(st)[1]
     if args.case != "probs":
-        summ, recs = qs.qs_profile(st)
         print(json.dumps({"case": args.case, "n": n, "blocks": [(kernel_name(r), round(r.ms, 4),
                           round(r.bytes / r.ms / 1e6, 1)) for r in recs]}))
     qs.qs_free_state(st)
@@ -573,6 +590,7 @@ def main():
     ap.add_argument("--case", choices=CASES, help="profiling aid: launch one kernel kind only")
     ap.add_argument("--n", type=int, default=26)
     ap.add_argument("--launches", type=int, default=3)
+    ap.add_argument("--tc-rows", type=int, default=0, help="threads per group of the FP16 tensor-core kernel (--case)")
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
     ap.add_argument("--tc-precision", type=int, default=0, help="tensor-core operands: 0 two FP16 halves, 1 3xTF32")
     ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32"],

@@ -115,7 +115,9 @@ typedef struct {
   int tile_bits;        /* QS_TILE: qubits per shared-memory tile, 0 = 64 KiB of amplitudes
                            (13 for c64, 12 for c128); 8..14 c64, 8..13 c128 */
   int tile_k;           /* QS_TILE: fusion width inside a tile, 0 = 3; 1..4 */
-  int reserved[2];
+  int tc_row_threads;   /* QS_TC with FP16 halves: threads sharing one group (row): 1, 2 or 4
+                           (4 acts as 2 below 5 targets); 0 = 2 for 6-target blocks, else 1 */
+  int reserved[1];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

@@ -64,7 +64,8 @@ class qs_opts(ctypes.Structure):
                 ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
                 ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
                 ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
-                ("tile_k", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("tile_k", ctypes.c_int), ("tc_row_threads", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class qs_class_table(ctypes.Structure):

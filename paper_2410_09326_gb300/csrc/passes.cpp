@@ -569,6 +569,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     return QS_EUNSUPPORTED;
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+  if (opts.tc_row_threads < 0 || opts.tc_row_threads == 3 || opts.tc_row_threads > 4) {
+    err = "opts.tc_row_threads must be 0, 1, 2 or 4";
+    return QS_EINVAL;
+  }
   if (flags & QS_TILE) {
     const int tmax = c128 ? kMaxTileBits - 1 : kMaxTileBits;
     if (opts.tile_bits != 0 && (opts.tile_bits < 8 || opts.tile_bits > tmax)) {
@@ -705,6 +709,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   for (Block &b : plan) {
     b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= (tf32 ? 5 : 6);
     b.tc_tf32 = b.tc && tf32;
+    // two threads per group only pay off at k = 6, where one thread per
+    // group would need more registers than exist (measured on GB300)
+    b.tc_rows = opts.tc_row_threads != 0 ? opts.tc_row_threads : (b.k >= 6 ? 2 : 1);
+    if (b.tc_rows == 4 && b.k < 5) b.tc_rows = 2;  // a thread converts at least 4 amplitudes
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;

@@ -39,7 +39,7 @@ double class_prior_fraction(int cls) {
   double f;
   if (kind == 2) f = 0.80;
   else if (kind == 1) f = 0.85;
-  else if (tc) f = k <= 4 ? 0.90 : (k == 5 ? 0.86 : 0.44);
+  else if (tc) f = k <= 4 ? 0.90 : (k == 5 ? 0.86 : 0.74);
   else {
     static const double dense[8] = {0.95, 0.98, 0.97, 0.97, 0.64, 0.34, 0.10, 0.05};
     f = dense[k];

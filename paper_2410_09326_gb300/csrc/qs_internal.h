@@ -59,6 +59,7 @@ struct Block {
   int meta = 4;                   // 0 one-qubit, 1 two-qubit, 3 swap, 4 fused
   bool tc = false;
   bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
+  int tc_rows = 1;                // FP16 tensor-core kernel: threads per group (1 or 2)
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,

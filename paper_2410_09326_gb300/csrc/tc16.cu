@@ -51,16 +51,24 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// Resident CTAs per SM the register budget is sized for.
-template <int K> struct Tc16Occ {
-  static constexpr int value = K <= 4 ? 4 : (K == 5 ? 3 : 1);
+// Resident CTAs per SM the register budget is sized for (TPR threads per row).
+template <int K, int TPR> struct Tc16Occ {
+  static constexpr int value = TPR == 4 ? 1 : (K <= 4 ? 4 : (K == 5 ? 3 : 1));
 };
 
-template <int K>
-__global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
+// TPR threads share one row of A (one group): thread (h, r), r = tid % 128,
+// h = tid / 128, gathers and converts the amplitudes s in [h D/TPR,
+// (h+1) D/TPR) of group r and later reads the matching TMEM columns of lane r
+// (warps w and w + 4 see the same lane quadrant). The row's scale and norms
+// are combined through shared memory. More threads per row means fewer
+// registers per thread and more warps per SM to hide the gather latency.
+template <int K, int TPR>
+__global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR>::value)
     k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
                  int *__restrict__ err) {
+  constexpr int NT = kTcThreads * TPR;
   constexpr int D = 1 << K;                    // amplitudes per group
+  constexpr int DH = D / TPR;                  // amplitudes per thread
   constexpr int KR = 2 * D;                    // real K = N of the GEMM
   constexpr uint32_t A_BYTES = 128u * KR * 2u;
   constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
@@ -68,6 +76,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
   constexpr uint32_t LBO = 128u;               // K-adjacent core matrices
   constexpr uint32_t NCOLS = 2 * KR;           // large and small accumulators
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+  static_assert(DH % 4 == 0, "a thread converts whole 16-byte core-matrix rows");
 
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *sA_hi = smem;
@@ -75,11 +84,16 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
   unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
+  __shared__ float red_in[TPR > 1 ? 2 * NT : 1];   // (row max, row norm) partials of the inputs
+  __shared__ float red_out[TPR > 1 ? NT : 1];      // row norm partials of the outputs
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
+  const int r = tid & 127;   // row of A = TMEM lane
+  const int h = tid >> 7;    // which part of the row
+  const int s0 = h * DH;     // first amplitude of this thread's part
 
-  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += NT) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                  "r"(NCOLS));
@@ -101,47 +115,38 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
 #pragma unroll
   for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
   const bool pair = p.tq[0] == 0;
-  // this thread's row of A: 8-row group (tid / 8), row (tid % 8) of each core matrix
-  const uint32_t row_off = (uint32_t)(tid >> 3) * SBO + (uint32_t)(tid & 7) * 16u;
+  // this thread's row of A: 8-row group (r / 8), row (r % 8) of each core matrix
+  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
   uint32_t phase = 0;
   bool aborted = false;
 
-  long long tile = blockIdx.x;
-  float2 v[D];
-  uint64_t base = 0;
-  bool valid = false;
-  auto gather = [&](long long t, uint64_t &b, bool &ok) {
-    const long long g = t * kTcThreads + tid;
-    ok = t < p.n_tiles && g < p.n_groups;
-    b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
-    if (pair) {
-#pragma unroll
-      for (int s = 0; s < D; s += 2) {
-        uint64_t off = 0;
-#pragma unroll
-        for (int j = 1; j < K; j++)
-          if ((s >> j) & 1) off += d[j];
-        const float4 x = ok ? *reinterpret_cast<const float4 *>(a + b + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[s] = make_float2(x.x, x.y);
-        v[s + 1] = make_float2(x.z, x.w);
-      }
-    } else {
-#pragma unroll
-      for (int s = 0; s < D; s++) {
-        uint64_t off = 0;
-#pragma unroll
-        for (int j = 0; j < K; j++)
-          if ((s >> j) & 1) off += d[j];
-        v[s] = ok ? a[b + off] : make_float2(0.f, 0.f);
-      }
-    }
-  };
-  auto store = [&](uint64_t b, int s, float re, float im) {
+  auto offset = [&](int s) {
     uint64_t off = 0;
 #pragma unroll
     for (int j = 0; j < K; j++)
       if ((s >> j) & 1) off += d[j];
-    a[b + off] = make_float2(re, im);
+    return off;
+  };
+
+  long long tile = blockIdx.x;
+  float2 v[DH];
+  uint64_t base = 0;
+  bool valid = false;
+  auto gather = [&](long long t, uint64_t &b, bool &ok) {
+    const long long g = t * kTcThreads + r;
+    ok = t < p.n_tiles && g < p.n_groups;
+    b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
+    if (pair) {
+#pragma unroll
+      for (int u = 0; u < DH; u += 2) {
+        const float4 x = ok ? *reinterpret_cast<const float4 *>(a + b + offset(s0 + u)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = make_float2(x.x, x.y);
+        v[u + 1] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < DH; u++) v[u] = ok ? a[b + offset(s0 + u)] : make_float2(0.f, 0.f);
+    }
   };
   gather(tile, base, valid);
 
@@ -149,29 +154,41 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
     // row scale: largest component into [0.5, 1)
     float mx = 0.f, nin = 0.f;
 #pragma unroll
-    for (int s = 0; s < D; s++) {
-      mx = fmaxf(mx, fmaxf(fabsf(v[s].x), fabsf(v[s].y)));
-      nin = fmaf(v[s].x, v[s].x, fmaf(v[s].y, v[s].y, nin));
+    for (int u = 0; u < DH; u++) {
+      mx = fmaxf(mx, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+      nin = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, nin));
+    }
+    if constexpr (TPR > 1) {
+      red_in[2 * tid] = mx;
+      red_in[2 * tid + 1] = nin;
+      __syncthreads();
+#pragma unroll
+      for (int o = 1; o < TPR; o++) {
+        const int pt = (tid + o * kTcThreads) % NT;
+        mx = fmaxf(mx, red_in[2 * pt]);
+        nin += red_in[2 * pt + 1];
+      }
     }
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
     const float sc = ldexpf(1.f, -e);
     // hi/lo rows: amplitudes 4c..4c+3 fill the 16-byte row of core matrix c
 #pragma unroll
-    for (int c = 0; c < D / 4; c++) {
+    for (int cl = 0; cl < DH / 4; cl++) {
+      const int c = s0 / 4 + cl;
       float x[8];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        x[2 * u] = v[4 * c + u].x * sc;
-        x[2 * u + 1] = v[4 * c + u].y * sc;
+        x[2 * u] = v[4 * cl + u].x * sc;
+        x[2 * u + 1] = v[4 * cl + u].y * sc;
       }
       uint4 hi, lo;
       uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        const __half2 h = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
-        const float2 hf = __half22float2(h);
-        hp[u] = *reinterpret_cast<const uint32_t *>(&h);
+        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+        const float2 hf = __half22float2(hh);
+        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
         lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
       }
       *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
@@ -206,15 +223,16 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    const uint32_t col0 = (uint32_t)(2 * s0);  // this thread's first column
     // pass 1: norm of the computed group (large + small products), 16
     // columns (8 amplitudes) at a time to keep registers free
     float nout = 0.f;
 #pragma unroll
-    for (int h = 0; h < KR / 16; h++) {
+    for (int hh = 0; hh < 2 * DH / 16; hh++) {
       uint32_t rb[16], rs[16];
-      TmemLd<16>::run(lane_base + 16 * h, rb);
-      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      TmemLd<16>::run(lane_base + col0 + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + col0 + 16 * hh, rs);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
       for (int i = 0; i < 16; i++) {
@@ -222,34 +240,37 @@ __global__ void __launch_bounds__(kTcThreads, Tc16Occ<K>::value)
         nout = fmaf(y, y, nout);
       }
     }
+    if constexpr (TPR > 1) {
+      red_out[tid] = nout;
+      __syncthreads();
+#pragma unroll
+      for (int o = 1; o < TPR; o++) nout += red_out[(tid + o * kTcThreads) % NT];
+    }
     // unitary block: the group keeps its input norm (this also undoes the row scale)
     const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
     // pass 2: scale and store, 8 amplitudes per chunk
 #pragma unroll
-    for (int h = 0; h < KR / 16; h++) {
+    for (int hh = 0; hh < 2 * DH / 16; hh++) {
       uint32_t rb[16], rs[16];
-      TmemLd<16>::run(lane_base + 16 * h, rb);
-      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      TmemLd<16>::run(lane_base + col0 + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + col0 + 16 * hh, rs);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (cur_valid) {
         if (pair) {
 #pragma unroll
           for (int u = 0; u < 4; u++) {
-            const int s = 8 * h + 2 * u;
-            uint64_t off = 0;
-#pragma unroll
-            for (int j = 1; j < K; j++)
-              if ((s >> j) & 1) off += d[j];
+            const int sl = s0 + 8 * hh + 2 * u;
             float y[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) y[q] = (__uint_as_float(rb[4 * u + q]) + __uint_as_float(rs[4 * u + q])) * f;
-            *reinterpret_cast<float4 *>(a + cur_base + off) = make_float4(y[0], y[1], y[2], y[3]);
+            *reinterpret_cast<float4 *>(a + cur_base + offset(sl)) = make_float4(y[0], y[1], y[2], y[3]);
           }
         } else {
 #pragma unroll
           for (int u = 0; u < 8; u++)
-            store(cur_base, 8 * h + u, (__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
-                  (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
+            a[cur_base + offset(s0 + 8 * hh + u)] =
+                make_float2((__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
+                            (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
         }
       }
     }
@@ -270,7 +291,7 @@ template <int K> size_t tc16_smem_bytes() {
   return 2 * 128 * KR * 2 + 2 * KR * KR * 2;
 }
 
-template <int K>
+template <int K, int TPR>
 cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
   TcParam p;
   p.n_groups = 1ll << (n - K - b.nctrl);
@@ -287,15 +308,16 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc16<K, TPR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16<K>, kTcThreads, smem);
-    per_sm = occ > Tc16Occ<K>::value ? Tc16Occ<K>::value : occ;
+    const int occ = resident_ctas((const void *)k_dense_tc16<K, TPR>, kTcThreads * TPR, smem);
+    per_sm = occ > Tc16Occ<K, TPR>::value ? Tc16Occ<K, TPR>::value : occ;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms * per_sm;
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16<K><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16<K, TPR><<<(int)grid, kTcThreads * TPR, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -328,10 +350,15 @@ void tc16_build_b(const Block &b, void *out) {
 }
 
 cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
-  switch (b.k) {
-    case 4: return run_tc16<4>(a, n, b, dev_b, err, s);
-    case 5: return run_tc16<5>(a, n, b, dev_b, err, s);
-    case 6: return run_tc16<6>(a, n, b, dev_b, err, s);
+  switch (b.k * 8 + b.tc_rows) {
+    case 4 * 8 + 1: return run_tc16<4, 1>(a, n, b, dev_b, err, s);
+    case 4 * 8 + 2: return run_tc16<4, 2>(a, n, b, dev_b, err, s);
+    case 5 * 8 + 1: return run_tc16<5, 1>(a, n, b, dev_b, err, s);
+    case 5 * 8 + 2: return run_tc16<5, 2>(a, n, b, dev_b, err, s);
+    case 5 * 8 + 4: return run_tc16<5, 4>(a, n, b, dev_b, err, s);
+    case 6 * 8 + 1: return run_tc16<6, 1>(a, n, b, dev_b, err, s);
+    case 6 * 8 + 2: return run_tc16<6, 2>(a, n, b, dev_b, err, s);
+    case 6 * 8 + 4: return run_tc16<6, 4>(a, n, b, dev_b, err, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -123,6 +123,38 @@ def test_dense_block_every_target_class(dtype, k, tc):
         check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | tc, dtype)
 
 
+@pytest.mark.parametrize("rows", [1, 2, 4])
+@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("n", [12, 17])
+def test_tc_threads_per_group(n, k, rows):
+    """The FP16 tensor-core kernel with one or two threads per group (row):
+    high, low and bit-0 targets, a control outside the block, a partial last
+    tile (n = 12) and many tiles (n = 17), from a random state."""
+    rng = cg.SplitMix64(500 + 10 * k + n)
+    o = qs.qs_default_opts()
+    o.tc_row_threads = rows
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    for qubits in (list(range(n - k, n)), list(range(k)), [0] + list(range(n - k + 1, n))):
+        gates = []
+        for _ in range(2):
+            gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+            gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        outside = [q for q in range(n) if q not in qubits][0]
+        gates += [("ccx", [outside, qubits[0], qubits[-1]])]
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC, o)
+            _, recs = qs.qs_profile(st)
+            assert any(r.tc for r in recs)
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5
+
+
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_tiny_registers(n):
     rng = cg.SplitMix64(77 + n)
