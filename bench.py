@@ -165,6 +165,12 @@ def kernel_name(rec):
     return f"k_dense_k{rec.k}" + ("_tc" if rec.tc else "")
 
 
+def CALIBRATION_FLAGS(qs):
+    """Flag sets profiled once before the measured-profile arm."""
+    fused = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_DIAG | qs.QS_TC
+    return [fused | qs.QS_FUSE_K(k) for k in (4, 5, 6)] + [qs.QS_VSWAP | qs.QS_TILE]
+
+
 def run_ours(args):
     import torch
     import paper_2410_09326_gb300 as qs
@@ -182,16 +188,21 @@ def run_ours(args):
     st = qs.qs_alloc_state(n, qs.QS_C64, stream=stream)
     probs_host = None
 
+    used = []  # flags each circuit ran with in the last step (after PGO)
+
     def step(flags, profile):
         """One pass of the hot path over the three circuits; returns per-block
         records and the algorithmic bytes of the step."""
         recs, nbytes, h2d = [], 0.0, 0.0
-        for _, text in circuits:
+        used.clear()
+        for ci, (_, text) in enumerate(circuits):
             qs.qs_set_basis(st, 0)
             _, gates = qs.qs_parse_qasm(text)
-            qs.qs_apply_circuit(st, gates, flags | (qs.QS_PROFILE if profile else 0))
+            f = flags[ci] if isinstance(flags, list) else flags
+            qs.qs_apply_circuit(st, gates, f | (qs.QS_PROFILE if profile else 0))
             summ, r = qs.qs_profile(st, with_records=profile)
             recs += r
+            used.append(summ.flags_used)
             nbytes += summ.total_bytes + (8 << n) + (8 << n)  # + reduction read + basis reset write
             h2d += summ.h2d_bytes
             global_probs = qs.qs_measure_probs(st, measured)
@@ -235,9 +246,21 @@ def run_ours(args):
     # probabilities back (2^16 doubles per circuit)
     e2e_value = bytes_per_step * world / (wall_max / args.steps) / 1e9
 
+    rules_flags = list(used)
+
     # plain per-gate kernels on the same GPU (one warm-up, one timed pass)
     plain_ms, _, plain_recs, plain_bytes, _ = timed(PLAIN_FLAGS, 1, 1, False)
     plain_ms = max_over_ranks(plain_ms, world)
+
+    # measured-profile activator: profiled calibration runs of a few flag
+    # sets fill the state's kernel-class table, then every call picks its
+    # flags from it (Sec. III-A: profile, then compile with the chosen passes)
+    for f in CALIBRATION_FLAGS(qs):
+        step(f, True)
+    table = qs.qs_profile_classes(st)
+    pgo_flags = [qs.qs_pgo_select(n, qs.qs_parse_qasm(t)[1], table=table)[0] for _, t in circuits]
+    pgo_ms, _, _, pgo_bytes, _ = timed(pgo_flags, args.steps, 1, False)
+    pgo_ms = max_over_ranks(pgo_ms, world) / args.steps
 
     # dominant kernel of the optimised step, from its per-launch event times
     per = {}
@@ -271,6 +294,12 @@ def run_ours(args):
                    "n_qubits": n, "circuits": [c[0] for c in circuits],
                    "gates": [qs.qs_parse_qasm(t)[1].size for _, t in circuits],
                    "l2": "state 8 GiB >> 129 MB L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+        "rules_flags": [hex(f) for f in rules_flags],
+        "pgo_measured": {"ms_per_step": round(pgo_ms, 3), "flags": [hex(f) for f in pgo_flags],
+                         "gbs": round(pgo_bytes / args.steps / (pgo_ms * 1e-3) / 1e9, 1),
+                         "note": "flags chosen once per circuit by the measured-profile activator "
+                                 "(qs_pgo_select on the class table of profiled calibration runs); "
+                                 "not the headline"},
         "plain_ms_per_step": round(plain_ms, 3),
         "plain_gbs": round(plain_bytes / (plain_ms * 1e-3) / 1e9, 1),
         "speedup_vs_plain": round(plain_ms / ms_per_step, 2),

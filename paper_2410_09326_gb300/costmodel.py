@@ -12,13 +12,13 @@ import numpy as np
 
 import circuitgen as cg
 
-from . import (QS_C64, QS_DIAG, QS_FUSE, QS_FUSE_K, QS_PROFILE, QS_TC, QS_VSWAP, gates_to_array,
+from . import (QS_C64, QS_DIAG, QS_FUSE, QS_FUSE_K, QS_PROFILE, QS_TC, QS_TILE, QS_VSWAP, gates_to_array,
                qs_alloc_state, qs_apply_circuit, qs_block_features, qs_free_state, qs_profile,
                qs_set_basis)
 
 # flag sets profiled for training: every kernel class the selector can choose
 TRAIN_FLAGS = [0, QS_VSWAP] + [QS_VSWAP | QS_FUSE | QS_FUSE_K(k) | QS_DIAG for k in (2, 3, 4, 5, 6)] + \
-              [QS_VSWAP | QS_FUSE | QS_FUSE_K(k) | QS_DIAG | QS_TC for k in (4, 5)]
+              [QS_VSWAP | QS_FUSE | QS_FUSE_K(k) | QS_DIAG | QS_TC for k in (4, 5, 6)] + [QS_VSWAP | QS_TILE]
 
 
 def profile_blocks(n, gates, flags, state=None, repeats=1):

@@ -37,7 +37,8 @@ double class_prior_fraction(int cls) {
   const int kind = (cls % 32) / 8, k = cls % 8;
   const bool tc = (cls & 32) != 0, low = (cls & 64) != 0;
   double f;
-  if (kind == 2) f = 0.80;
+  if (kind == 3) f = 0.15;  // tile pass: bound by the member blocks' arithmetic, not by HBM
+  else if (kind == 2) f = 0.80;
   else if (kind == 1) f = 0.85;
   else if (tc) f = k <= 4 ? 0.90 : (k == 5 ? 0.86 : 0.74);
   else {
@@ -95,7 +96,7 @@ uint64_t rules_select(int n, const qs_gate *gates, size_t n_gates, const qs_opts
     }
   }
   (void)n;
-  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_FOLD | QS_RELOCATE | (15ull << 16));
+  uint64_t f = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_FOLD | QS_RELOCATE | QS_TILE | (15ull << 16));
   // rotation folding: T gates above the threshold share of all gates
   if (n_gates && (double)t_count / (double)n_gates > o.t_ratio) f |= QS_FOLD;
   // virtual swap: SWAP gates present, or two-qubit gates hitting the fast
@@ -155,8 +156,9 @@ void record_features(const qs_block_record &r, int n, bool c128, float *f) {
 namespace {
 
 // The flag sets both activators choose among: plain, virtual swap alone,
-// and fusion k = 1..6 with diagonal runs (tensor cores for k >= 4, c64).
-std::vector<uint64_t> candidate_flags(const qs_gate *gates, size_t n_gates, bool c128) {
+// fusion k = 1..6 with diagonal runs (tensor cores for k >= 4, c64), and
+// cache-blocked tile passes when the state is wider than one tile.
+std::vector<uint64_t> candidate_flags(int n, const qs_gate *gates, size_t n_gates, bool c128, const qs_opts &o) {
   bool has_swap = false;
   for (size_t i = 0; i < n_gates; i++) has_swap |= gates[i].op == QS_SWAP;
   std::vector<uint64_t> cands;
@@ -167,6 +169,7 @@ std::vector<uint64_t> candidate_flags(const qs_gate *gates, size_t n_gates, bool
     cands.push_back(vs | QS_FUSE | QS_FUSE_K(k) | QS_DIAG);
     if (k >= 4 && !c128) cands.push_back(vs | QS_FUSE | QS_FUSE_K(k) | QS_DIAG | QS_TC);
   }
+  if (n > tile_bits_of(o, c128)) cands.push_back(vs | QS_TILE);
   return cands;
 }
 
@@ -174,7 +177,7 @@ std::vector<uint64_t> candidate_flags(const qs_gate *gates, size_t n_gates, bool
 
 qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
                      uint64_t *flags_out, double *pred_ms, std::string &err) {
-  const std::vector<uint64_t> cands = candidate_flags(gates, n_gates, c128);
+  const std::vector<uint64_t> cands = candidate_flags(n, gates, n_gates, c128, o);
   std::vector<float> feats;
   std::vector<size_t> first(cands.size() + 1, 0);
   std::vector<Block> plan;
@@ -220,9 +223,9 @@ qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t 
 qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
                           const qs_class_table *t, uint64_t base, uint64_t *flags_out, double *pred_ms,
                           std::string &err) {
-  const uint64_t keep = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_TC | (15ull << 16) |
+  const uint64_t keep = base & ~(uint64_t)(QS_VSWAP | QS_FUSE | QS_DIAG | QS_TC | QS_TILE | (15ull << 16) |
                                            QS_PGO_RULES | QS_PGO_MEASURED);
-  const std::vector<uint64_t> cands = candidate_flags(gates, n_gates, c128);
+  const std::vector<uint64_t> cands = candidate_flags(n, gates, n_gates, c128, o);
   const double peak = o.peak_gbs > 0 ? o.peak_gbs : 6688.8;
   double best = 1e300;
   uint64_t best_f = cands[0];

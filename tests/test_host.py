@@ -283,7 +283,7 @@ def test_measured_select_follows_the_table():
     for cls in range(qs.QS_N_CLASSES):
         kind, k, tc = (cls % 32) // 8, cls % 8, bool(cls & 32)
         gbs = 6000.0
-        if tc:
+        if tc or kind == 3:
             gbs = 300.0
         elif kind == 0 and k >= 4:
             gbs = 500.0
@@ -454,3 +454,22 @@ def test_qft_diagonal_ladders_become_polynomials():
     # states of at most 10 qubits keep phase tables
     recs10 = qs.qs_plan(10, qs.gates_to_array(cg.qft(10, x=5)[0]), qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG)[0]
     assert not any(r.kind == 4 for r in recs10)
+
+
+def test_measured_select_picks_tile_passes_when_they_measured_fast():
+    """Cache-blocked passes are a candidate of the measured-profile activator:
+    chosen when the table says tile passes move bytes at HBM speed, not with
+    the compiled-in priors (their CUDA-core arithmetic is the bound)."""
+    c = cg.config1_circuits(n=30)
+    n, gates = c["random"]
+    arr = qs.gates_to_array(gates)
+    flags, _ = qs.qs_pgo_select(n, arr)
+    assert not flags & qs.QS_TILE
+    t = qs.qs_class_table()
+    for cls in range(qs.QS_N_CLASSES):
+        kind = (cls % 32) // 8
+        t.bytes[cls] = (6500.0 if kind == 3 else 5000.0) * 1e6
+        t.ms[cls] = 1.0
+        t.count[cls] = 1
+    flags, ms = qs.qs_pgo_select(n, arr, table=t)
+    assert flags & qs.QS_TILE and flags & qs.QS_VSWAP
