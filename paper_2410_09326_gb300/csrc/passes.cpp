@@ -569,6 +569,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     return QS_EUNSUPPORTED;
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+  if (opts.tc_gather < 0 || opts.tc_gather > 2) {
+    err = "opts.tc_gather out of range (0..2)";
+    return QS_EINVAL;
+  }
   if (opts.tc_row_threads < 0 || opts.tc_row_threads == 3 || opts.tc_row_threads > 4) {
     err = "opts.tc_row_threads must be 0, 1, 2 or 4";
     return QS_EINVAL;
@@ -713,6 +717,9 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     // group would need more registers than exist (measured on GB300)
     b.tc_rows = opts.tc_row_threads != 0 ? opts.tc_row_threads : (b.k >= 6 ? 2 : 1);
     if (b.tc_rows == 4 && b.k < 5) b.tc_rows = 2;  // a thread converts at least 4 amplitudes
+    // staging tiles through shared memory measured slower than per-thread
+    // gathers on GB300 (4.0 vs 6.3 TB/s at 5 targets), so it is opt-in
+    b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;

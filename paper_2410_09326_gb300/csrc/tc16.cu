@@ -286,6 +286,323 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR>::value)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
+// Staged variant (K = 4, 5; bit 0 not a control): a tile of 128 groups is
+// the sub-cube of the index space spanned by the 7 lowest free bits and the
+// K targets (the other bits fixed per tile). Bits 0..6 always lie in it, so
+// in address order the tile is made of contiguous runs of at least 1 KiB,
+// whatever the targets: the CTA copies it into shared memory with 16-byte
+// cp.async in address order (the next tile's copies fly during the MMAs and
+// the epilogue), each thread then reads its group's row from a layout in
+// which consecutive rows are consecutive words, and the results leave the
+// same way through the (by then idle) A buffers. Element e of the tile (its
+// local index, bit j = j-th lowest bit of the sub-cube) sits at global offset
+// dep_lo[e & 63] + dep_hi[e >> 6] from the tile base and at staging slot
+// slot_lo[e & 63] + slot_hi[e >> 6], slot(r, s) = 128 s + r, or
+// 256 (s >> 1) + 2 r + (s & 1) when bit 0 is a target (pairs stay adjacent).
+struct TcStageParam {
+  long long n_tiles;
+  unsigned long long cmask;
+  int nhi;                        // free bits above the 7 lowest: the tile index
+  int hi_pos[40];
+  int pair;                       // bit 0 is target 0
+  int withhold_commit;
+  unsigned long long dep_lo[64], dep_hi[64];
+  unsigned short slot_lo[64], slot_hi[64];
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+template <int K>
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_dense_tc16s(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcStageParam p,
+                  int *__restrict__ err) {
+  constexpr int D = 1 << K;
+  constexpr int KR = 2 * D;
+  constexpr int ELEMS = 128 * D;                 // amplitudes per tile
+  constexpr int LB = 7 + K;                      // local index bits
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t NCOLS = 2 * KR;
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+  static_assert(2 * A_BYTES == ELEMS * 8u, "the A buffers hold one tile of outputs");
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA_hi = smem;
+  unsigned char *sA_lo = smem + A_BYTES;
+  float2 *sOut = reinterpret_cast<float2 *>(smem);            // A buffers, reused for the outputs
+  unsigned char *sB = smem + 2 * A_BYTES;                     // hi then lo
+  float2 *sIn = reinterpret_cast<float2 *>(smem + 2 * A_BYTES + 2 * B_BYTES);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ unsigned long long dep_lo[64], dep_hi[64];
+  __shared__ unsigned short slot_lo[64], slot_hi[64];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (tid < 64) {
+    dep_lo[tid] = p.dep_lo[tid];
+    dep_hi[tid] = p.dep_hi[tid];
+    slot_lo[tid] = p.slot_lo[tid];
+    slot_hi[tid] = p.slot_hi[tid];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t mbar_a = smem_addr(&mbar);
+  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+  const uint32_t in_addr = smem_addr(sIn);
+  const int r = tid;
+  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+  const bool pair = p.pair != 0;
+
+  auto tile_base = [&](long long t) {
+    uint64_t b = p.cmask;
+    for (int j = 0; j < p.nhi; j++) b |= (uint64_t)((t >> j) & 1) << p.hi_pos[j];
+    return b;
+  };
+  auto issue_loads = [&](long long t) {
+    const uint64_t tb = tile_base(t);
+#pragma unroll 4
+    for (int e = 2 * tid; e < ELEMS; e += 2 * kTcThreads) {
+      const uint64_t off = tb + dep_lo[e & 63] + dep_hi[e >> 6];
+      const uint32_t slot = (uint32_t)slot_lo[e & 63] + slot_hi[e >> 6];
+      cp_async16(in_addr + slot * 8u, a + off);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  uint32_t phase = 0;
+  bool aborted = false;
+  long long tile = blockIdx.x;
+  if (tile < p.n_tiles) issue_loads(tile);
+  for (; tile < p.n_tiles; tile += gridDim.x) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // this thread's group (row r) out of the staged tile
+    float2 v[D];
+    if (pair) {
+#pragma unroll
+      for (int s = 0; s < D; s += 2) {
+        const float4 x = *reinterpret_cast<const float4 *>(sIn + (s >> 1) * 256 + 2 * r);
+        v[s] = make_float2(x.x, x.y);
+        v[s + 1] = make_float2(x.z, x.w);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < D; s++) v[s] = sIn[s * 128 + r];
+    }
+    float mx = 0.f, nin = 0.f;
+#pragma unroll
+    for (int s = 0; s < D; s++) {
+      mx = fmaxf(mx, fmaxf(fabsf(v[s].x), fabsf(v[s].y)));
+      nin = fmaf(v[s].x, v[s].x, fmaf(v[s].y, v[s].y, nin));
+    }
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    const float sc = ldexpf(1.f, -ex);
+#pragma unroll
+    for (int c = 0; c < D / 4; c++) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        x[2 * u] = v[4 * c + u].x * sc;
+        x[2 * u + 1] = v[4 * c + u].y * sc;
+      }
+      uint4 hi, lo;
+      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+        const float2 hf = __half22float2(hh);
+        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
+        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
+      *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ks++) {
+        const uint32_t koff = (uint32_t)ks * 2u * LBO;
+        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+        mma_f16(tmem, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
+        mma_f16(tmem + KR, dah, dbl, IDESC, ks > 0 ? 1u : 0u);
+        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+      }
+      if (!p.withhold_commit) mma_commit(mbar_a);
+    }
+    // every row has been read out of the staging buffer: refill it
+    const uint64_t cur_base = tile_base(tile);
+    if (tile + gridDim.x < p.n_tiles) issue_loads(tile + gridDim.x);
+    const bool ok = mbar_wait(mbar_a, phase);
+    phase ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      aborted = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    float nout = 0.f;
+#pragma unroll
+    for (int h = 0; h < KR / 16; h++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * h, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+    // outputs into the A buffers (the MMAs that read them have completed)
+#pragma unroll
+    for (int h = 0; h < KR / 16; h++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * h, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * h, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        const int s = 8 * h + u;
+        const float2 y = make_float2((__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
+                                     (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
+        if (pair) sOut[(s >> 1) * 256 + 2 * r + (s & 1)] = y;
+        else sOut[s * 128 + r] = y;
+      }
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int e = 2 * tid; e < ELEMS; e += 2 * kTcThreads) {
+      const uint64_t off = cur_base + dep_lo[e & 63] + dep_hi[e >> 6];
+      const uint32_t slot = (uint32_t)slot_lo[e & 63] + slot_hi[e >> 6];
+      *reinterpret_cast<float4 *>(a + off) = *reinterpret_cast<const float4 *>(sOut + slot);
+    }
+    // the next iteration's barrier orders these reads before A is rewritten
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) {
+    if (tid == 0) mma_commit(mbar_a);
+    mbar_wait(mbar_a, phase ^ 1);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+  (void)LB;
+}
+
+// Host tables of the staged kernel; false when the block does not qualify
+// (bit 0 a control, or fewer than 7 free bits).
+bool stage_param(int n, const Block &b, TcStageParam &p) {
+  std::memset(&p, 0, sizeof(p));
+  uint64_t fixed = b.cmask;
+  for (int j = 0; j < b.k; j++) fixed |= 1ull << b.q[j];
+  if (b.cmask & 1ull) return false;
+  int freep[64], nfree = 0;
+  for (int q = 0; q < n; q++)
+    if (!((fixed >> q) & 1)) freep[nfree++] = q;
+  if (nfree < 7) return false;
+  p.pair = b.q[0] == 0 ? 1 : 0;
+  // sub-cube bits in ascending order: 7 lowest free bits and the targets
+  int pos[16], np = 0, rbit[16], sbit[16];
+  uint64_t cube = 0;
+  for (int j = 0; j < 7; j++) cube |= 1ull << freep[j];
+  for (int j = 0; j < b.k; j++) cube |= 1ull << b.q[j];
+  for (int q = 0; q < 64; q++)
+    if ((cube >> q) & 1) {
+      pos[np] = q;
+      rbit[np] = -1;
+      sbit[np] = -1;
+      for (int j = 0; j < 7; j++)
+        if (freep[j] == q) rbit[np] = j;
+      for (int j = 0; j < b.k; j++)
+        if (b.q[j] == q) sbit[np] = j;
+      np++;
+    }
+  auto slot_of_bit = [&](int j) -> uint32_t {
+    if (rbit[j] >= 0) return p.pair ? (2u << rbit[j]) : (1u << rbit[j]);
+    const int sb = sbit[j];
+    if (!p.pair) return 128u << sb;
+    return sb == 0 ? 1u : (256u << (sb - 1));
+  };
+  for (int x = 0; x < 64; x++) {
+    uint64_t dl = 0, dh = 0;
+    uint32_t sl = 0, sh = 0;
+    for (int j = 0; j < 6 && j < np; j++)
+      if ((x >> j) & 1) {
+        dl |= 1ull << pos[j];
+        sl += slot_of_bit(j);
+      }
+    for (int j = 6; j < np && j < 12; j++)
+      if ((x >> (j - 6)) & 1) {
+        dh |= 1ull << pos[j];
+        sh += slot_of_bit(j);
+      }
+    p.dep_lo[x] = dl;
+    p.dep_hi[x] = dh;
+    p.slot_lo[x] = (unsigned short)sl;
+    p.slot_hi[x] = (unsigned short)sh;
+  }
+  p.nhi = 0;
+  for (int j = 7; j < nfree; j++) p.hi_pos[p.nhi++] = freep[j];
+  p.n_tiles = 1ll << p.nhi;
+  p.cmask = b.cmask;
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
+  return true;
+}
+
+template <int K> size_t tc16s_smem_bytes() {
+  constexpr size_t KR = 2 << K;
+  return 2 * 128 * KR * 2 + 2 * KR * KR * 2 + (size_t)128 * (1 << K) * 8;
+}
+
+template <int K>
+cudaError_t run_tc16s(float2 *a, const TcStageParam &p, const void *dev_b, int *err, cudaStream_t s) {
+  const size_t smem = tc16s_smem_bytes<K>();
+  static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16s<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc16s<K>, kTcThreads, smem);
+    // TMEM: 2 x 128 columns (K = 5) or 4 x 64 (K = 4) stay within 512 per SM
+    const int cap = K == 5 ? 2 : 4;
+    per_sm = occ > cap ? cap : occ;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms * per_sm;
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16s<K><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
 template <int K> size_t tc16_smem_bytes() {
   constexpr size_t KR = 2 << K;
   return 2 * 128 * KR * 2 + 2 * KR * KR * 2;
@@ -350,6 +667,10 @@ void tc16_build_b(const Block &b, void *out) {
 }
 
 cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+  if (b.tc_staged && (b.k == 4 || b.k == 5)) {
+    static thread_local TcStageParam sp;  // large: kept off the stack; the launch copies it
+    if (stage_param(n, b, sp)) return b.k == 4 ? run_tc16s<4>(a, sp, dev_b, err, s) : run_tc16s<5>(a, sp, dev_b, err, s);
+  }
   switch (b.k * 8 + b.tc_rows) {
     case 4 * 8 + 1: return run_tc16<4, 1>(a, n, b, dev_b, err, s);
     case 4 * 8 + 2: return run_tc16<4, 2>(a, n, b, dev_b, err, s);
