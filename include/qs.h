@@ -117,8 +117,11 @@ typedef struct {
   int tile_k;           /* QS_TILE: fusion width inside a tile, 0 = 3; 1..4 */
   int tc_row_threads;   /* QS_TC with FP16 halves: threads sharing one group (row): 1, 2 or 4
                            (4 acts as 2 below 5 targets); 0 = 2 for 6-target blocks, else 1 */
-  int tc_gather;        /* QS_TC with FP16 halves, 4 and 5 targets: 0 = default (2), 1 = tiles
-                           staged through shared memory in address order, 2 = per-thread gathers */
+  int tc_gather;        /* QS_TC with FP16 halves: 0 = default (2); 1 = tiles staged through shared
+                           memory in address order (4, 5 targets); 2 = per-thread gathers, next
+                           tile gathered during the MMAs; 3 = per-thread gathers without that
+                           prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
+                           2 at 6) */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);
