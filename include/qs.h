@@ -122,6 +122,11 @@ typedef struct {
                            tile gathered during the MMAs; 3 = per-thread gathers without that
                            prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
                            2 at 6) */
+  int fuse_lookahead;   /* fusion: where a gate could join several blocks or open a new one,
+                           each choice is followed by this many gates of first-fit placement
+                           and the one leaving the fewest blocks is taken; 0 = first fit
+                           (qs_default_opts: 60) */
+  int reserved[3];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

@@ -65,7 +65,8 @@ class qs_opts(ctypes.Structure):
                 ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
                 ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
                 ("tile_k", ctypes.c_int), ("tc_row_threads", ctypes.c_int),
-                ("tc_gather", ctypes.c_int)]
+                ("tc_gather", ctypes.c_int), ("fuse_lookahead", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class qs_class_table(ctypes.Structure):

@@ -213,6 +213,7 @@ void qs_default_opts(qs_opts *o) {
   o->diag_max = QS_MAX_DIAG;
   o->threads = 0;
   o->peak_gbs = 6688.8;
+  o->fuse_lookahead = 60;
 }
 
 const char *qs_last_error(void) { return last_error_ref().c_str(); }

@@ -140,6 +140,102 @@ void greedy_groups(const std::vector<qs_gate> &pg, const std::vector<int> &idx, 
   }
 }
 
+// Fusion with a roll-out look-ahead (a pilot method): where a gate could join
+// several blocks (the first four that fit) or open a new one, each choice is
+// followed by `horizon` gates of plain first-fit placement, and the choice
+// whose roll-out ends with the fewest blocks -- then the narrowest recent
+// blocks -- is kept; ties keep the earliest candidate (first fit). Placement
+// obeys the same commutation rule and width limits as greedy_groups.
+// limit(all_diag_block_and_gate) is the width bound.
+template <typename Limit>
+void lookahead_groups(const std::vector<qs_gate> &pg, const std::vector<int> &idx, std::vector<Pending> &groups,
+                      Limit limit, int horizon) {
+  struct LG {
+    uint64_t qmask;
+    bool all_diag;
+  };
+  struct GI {
+    uint64_t gmask;
+    bool gdiag;
+    int nq;
+    int q[6];
+    bool dq[6];
+  };
+  const int N = (int)idx.size();
+  std::vector<GI> info(N);
+  for (int i = 0; i < N; i++) {
+    const qs_gate &g = pg[idx[i]];
+    GI &x = info[i];
+    x.gmask = 0;
+    x.gdiag = op_info(g.op).diagonal;
+    x.nq = g.nq;
+    for (int j = 0; j < g.nq; j++) {
+      x.q[j] = g.q[j];
+      x.dq[j] = gate_diag_on(g, j);
+      x.gmask |= 1ull << g.q[j];
+    }
+  }
+  auto lower_of = [](const GI &x, const int *la, const int *ln) {
+    int lower = -1;
+    for (int j = 0; j < x.nq; j++) lower = std::max(lower, x.dq[j] ? ln[x.q[j]] : la[x.q[j]]);
+    return lower;
+  };
+  auto fits = [&](const LG &b, const GI &x) {
+    return popcount64(b.qmask | x.gmask) <= limit(b.all_diag && x.gdiag);
+  };
+  auto place = [](std::vector<LG> &G, int *la, int *ln, const GI &x, int ch) {
+    if (ch == (int)G.size()) G.push_back({0, true});
+    G[ch].qmask |= x.gmask;
+    G[ch].all_diag = G[ch].all_diag && x.gdiag;
+    for (int j = 0; j < x.nq; j++) {
+      la[x.q[j]] = std::max(la[x.q[j]], ch);
+      if (!x.dq[j]) ln[x.q[j]] = std::max(ln[x.q[j]], ch);
+    }
+  };
+  std::vector<LG> G, G2;
+  int la[64], ln[64], la2[64], ln2[64];
+  for (int q = 0; q < 64; q++) la[q] = ln[q] = -1;
+  for (int i = 0; i < N; i++) {
+    const GI &x = info[i];
+    const int lower = std::max(lower_of(x, la, ln), 0);
+    int cand[5], nc = 0;
+    for (int b = lower; b < (int)G.size() && nc < 4; b++)
+      if (fits(G[b], x)) cand[nc++] = b;
+    cand[nc++] = (int)G.size();
+    int ch = cand[0];
+    if (nc > 1 && horizon > 0) {
+      long best_blocks = -1, best_tail = 0;
+      for (int c = 0; c < nc; c++) {
+        G2 = G;
+        std::memcpy(la2, la, sizeof(la));
+        std::memcpy(ln2, ln, sizeof(ln));
+        place(G2, la2, ln2, x, cand[c]);
+        const int end = std::min(N, i + 1 + horizon);
+        for (int j = i + 1; j < end; j++) {
+          const GI &y = info[j];
+          int b = std::max(lower_of(y, la2, ln2), 0);
+          while (b < (int)G2.size() && !fits(G2[b], y)) b++;
+          place(G2, la2, ln2, y, b);
+        }
+        long tail = 0;
+        for (int b = std::max(0, (int)G2.size() - 6); b < (int)G2.size(); b++) tail += popcount64(G2[b].qmask);
+        if (best_blocks < 0 || (long)G2.size() < best_blocks ||
+            ((long)G2.size() == best_blocks && tail < best_tail)) {
+          best_blocks = (long)G2.size();
+          best_tail = tail;
+          ch = cand[c];
+        }
+      }
+    }
+    place(G, la, ln, x, ch);
+    if (ch == (int)groups.size()) groups.emplace_back();
+    Pending &p = groups[ch];
+    p.members.push_back(idx[i]);
+    p.qmask |= x.gmask;
+    p.all_diag = p.all_diag && x.gdiag;
+  }
+}
+
 // Qubits on which the gate is the identity whenever that qubit is 0 (the
 // controls of a controlled gate; both qubits of CZ / CPhase; the qubit of a
 // phase gate diag(1, e^{ia})). A block made only of such gates on a qubit has
@@ -690,12 +786,17 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     // polynomial (states of at least 11 qubits, which the kernel needs)
     const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
     const int dlimit = phase_ok ? 64 : D;
+    auto limit = [&](bool nd) { return nd ? (dfuse ? dlimit : std::max(K, 1)) : K; };
     greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
-      const int width = popcount64(p.qmask | gmask);
-      const bool nd = p.all_diag && gdiag;
-      const int limit = nd ? (dfuse ? dlimit : std::max(K, 1)) : K;
-      return width <= limit;
+      return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
     });
+    if (opts.fuse_lookahead > 0) {
+      // the roll-out heuristic usually saves blocks but is not guaranteed
+      // to: keep whichever grouping launches fewer
+      std::vector<Pending> alt;
+      lookahead_groups(pg, all, alt, limit, opts.fuse_lookahead);
+      if (alt.size() < groups.size()) groups.swap(alt);
+    }
   }
 
   // (3) products and classification

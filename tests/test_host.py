@@ -264,7 +264,7 @@ def test_measured_select_with_priors_prefers_wide_tensor_core_blocks():
     n, gates = c["random"]
     flags, ms = qs.qs_pgo_select(n, qs.gates_to_array(gates))
     assert flags & qs.QS_VSWAP and flags & qs.QS_FUSE and flags & qs.QS_TC
-    assert (flags >> 16) & 15 in (4, 5)
+    assert (flags >> 16) & 15 in (4, 5, 6)
     assert 100 < ms < 5000
     # GHZ has no SWAP: no virtual swap in the choice
     n, gates = c["ghz"]
