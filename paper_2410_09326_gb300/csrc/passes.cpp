@@ -84,6 +84,14 @@ template <typename F> void parallel_for(size_t n, F f) {
   for (auto &x : th) x.join();
 }
 
+// f(0..n) for a handful of independent tasks, one host thread each.
+template <typename F> void run_tasks(size_t n, F f) {
+  std::vector<std::thread> th;
+  for (size_t i = 1; i < n; i++) th.emplace_back([&f, i] { f(i); });
+  if (n > 0) f(0);
+  for (auto &t : th) t.join();
+}
+
 struct Pending {
   std::vector<int> members;  // indices into the physical gate list
   uint64_t qmask = 0;
@@ -787,15 +795,29 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
     const int dlimit = phase_ok ? 64 : D;
     auto limit = [&](bool nd) { return nd ? (dfuse ? dlimit : std::max(K, 1)) : K; };
-    greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
-      return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
-    });
     if (opts.fuse_lookahead > 0) {
       // the roll-out heuristic usually saves blocks but is not guaranteed
-      // to: keep whichever grouping launches fewer
-      std::vector<Pending> alt;
-      lookahead_groups(pg, all, alt, limit, opts.fuse_lookahead);
-      if (alt.size() < groups.size()) groups.swap(alt);
+      // to, and its best horizon varies: plain first fit and roll-outs of
+      // L and 4L/3 gates run side by side, the grouping with the fewest
+      // blocks is launched (earliest of them on a tie)
+      std::vector<Pending> alt[3];
+      const int horizons[3] = {0, opts.fuse_lookahead, opts.fuse_lookahead + opts.fuse_lookahead / 3};
+      run_tasks(3, [&](size_t v) {
+        if (v == 0)
+          greedy_groups(pg, all, alt[0], [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
+            return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
+          });
+        else
+          lookahead_groups(pg, all, alt[v], limit, horizons[v]);
+      });
+      int best = 0;
+      for (int v = 1; v < 3; v++)
+        if (alt[v].size() < alt[best].size()) best = v;
+      groups.swap(alt[best]);
+    } else {
+      greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
+        return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
+      });
     }
   }
 
