@@ -473,3 +473,24 @@ def test_measured_select_picks_tile_passes_when_they_measured_fast():
         t.count[cls] = 1
     flags, ms = qs.qs_pgo_select(n, arr, table=t)
     assert flags & qs.QS_TILE and flags & qs.QS_VSWAP
+
+
+def test_lookahead_fusion_never_adds_blocks_and_saves_them_on_layered_circuits():
+    """The roll-out search keeps first fit's grouping unless it finds one with
+    fewer blocks; on the layered random circuits it does (the measured step
+    time follows the block count, each block being one HBM pass)."""
+    c = cg.config1_circuits(n=30)
+    arr = qs.gates_to_array(c["random"][1])
+    first = qs.qs_default_opts()
+    first.fuse_lookahead = 0
+    for k in (4, 5, 6):
+        flags = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG
+        base = len(qs.qs_plan(30, arr, flags, opts=first)[0])
+        searched = len(qs.qs_plan(30, arr, flags)[0])
+        assert searched <= base
+        if k >= 5:
+            assert searched <= 0.9 * base, (k, searched, base)
+    for name in ("ghz", "qft"):
+        arr = qs.gates_to_array(c[name][1])
+        flags = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG
+        assert len(qs.qs_plan(30, arr, flags)[0]) <= len(qs.qs_plan(30, arr, flags, opts=first)[0])
