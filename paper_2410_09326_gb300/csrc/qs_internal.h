@@ -61,7 +61,7 @@ struct Block {
   bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
   int tc_rows = 1;                // FP16 tensor-core kernel: threads per group (1 or 2)
   bool tc_staged = false;         // FP16 tensor-core kernel: tiles staged through shared memory
-  bool tc_prefetch = true;        // FP16 tensor-core kernel: next tile gathered during the MMAs
+  int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,

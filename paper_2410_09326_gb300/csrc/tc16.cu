@@ -52,11 +52,15 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 }
 
 // Resident CTAs per SM the register budget is sized for (TPR threads per row).
-// Without the one-tile-ahead register prefetch (PF = false) a thread needs
-// fewer registers, so more CTAs fit and they hide each other's gathers.
-template <int K, int TPR, bool PF = true> struct Tc16Occ {
+// PFD = tiles gathered ahead into registers (0, 1 or 2). Without the
+// prefetch a thread needs fewer registers, so more CTAs fit and they hide
+// each other's gathers; two tiles ahead keep loads in flight across a whole
+// tile at the price of registers.
+template <int K, int TPR, int PFD = 1> struct Tc16Occ {
   static constexpr int value =
-      TPR == 4 ? 1 : (PF ? (K <= 4 ? 4 : (K == 5 ? 3 : 1)) : (K <= 4 ? 6 : (K == 5 ? 4 : 1)));
+      TPR == 4 ? 1
+               : (PFD == 1 ? (K <= 4 ? 4 : (K == 5 ? 3 : 1))
+                           : (PFD == 0 ? (K <= 4 ? 6 : (K == 5 ? 4 : 1)) : (K <= 4 ? 3 : (K == 5 ? 2 : 1))));
 };
 
 // TPR threads share one row of A (one group): thread (h, r), r = tid % 128,
@@ -65,8 +69,8 @@ template <int K, int TPR, bool PF = true> struct Tc16Occ {
 // (warps w and w + 4 see the same lane quadrant). The row's scale and norms
 // are combined through shared memory. More threads per row means fewer
 // registers per thread and more warps per SM to hide the gather latency.
-template <int K, int TPR, bool PF>
-__global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PF>::value)
+template <int K, int TPR, int PFD>
+__global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
     k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
                  int *__restrict__ err) {
   constexpr int NT = kTcThreads * TPR;
@@ -132,10 +136,10 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PF>::value)
   };
 
   long long tile = blockIdx.x;
-  float2 v[DH];
-  uint64_t base = 0;
-  bool valid = false;
-  auto gather = [&](long long t, uint64_t &b, bool &ok) {
+  float2 v[DH], v2[PFD == 2 ? DH : 1];
+  uint64_t base = 0, base2 = 0;
+  bool valid = false, valid2 = false;
+  auto gather = [&](long long t, uint64_t &b, bool &ok, float2 *v) {
     const long long g = t * kTcThreads + r;
     ok = t < p.n_tiles && g < p.n_groups;
     b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
@@ -151,10 +155,11 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PF>::value)
       for (int u = 0; u < DH; u++) v[u] = ok ? a[b + offset(s0 + u)] : make_float2(0.f, 0.f);
     }
   };
-  if (PF) gather(tile, base, valid);
+  if (PFD >= 1) gather(tile, base, valid, v);
+  if (PFD == 2) gather(tile + gridDim.x, base2, valid2, v2);
 
   for (; tile < p.n_tiles; tile += gridDim.x) {
-    if (!PF) gather(tile, base, valid);
+    if (PFD == 0) gather(tile, base, valid, v);
     // row scale: largest component into [0.5, 1)
     float mx = 0.f, nin = 0.f;
 #pragma unroll
@@ -218,7 +223,16 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PF>::value)
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
-    if (PF) gather(tile + gridDim.x, base, valid);  // next tile, in flight during the MMAs
+    if (PFD == 1) gather(tile + gridDim.x, base, valid, v);  // next tile, in flight during the MMAs
+    if (PFD == 2) {
+      // the tile after next goes in flight; the next one (loaded during the
+      // previous tile) moves into place
+#pragma unroll
+      for (int u = 0; u < DH; u++) v[u] = v2[u];
+      base = base2;
+      valid = valid2;
+      gather(tile + 2 * (long long)gridDim.x, base2, valid2, v2);
+    }
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -612,7 +626,7 @@ template <int K> size_t tc16_smem_bytes() {
   return 2 * 128 * KR * 2 + 2 * KR * KR * 2;
 }
 
-template <int K, int TPR, bool PF = true>
+template <int K, int TPR, int PFD = 1>
 cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
   TcParam p;
   p.n_groups = 1ll << (n - K - b.nctrl);
@@ -630,18 +644,18 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   cudaGetDevice(&dev);
   if (configured != dev) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_dense_tc16<K, TPR, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dense_tc16<K, TPR, PFD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16<K, TPR, PF>, kTcThreads * TPR, smem);
+    const int occ = resident_ctas((const void *)k_dense_tc16<K, TPR, PFD>, kTcThreads * TPR, smem);
     // TMEM: at most 512 columns per SM (2 x KR columns per CTA)
     const int tmem_cap = 512 / (4 << K);
-    per_sm = occ > Tc16Occ<K, TPR, PF>::value ? Tc16Occ<K, TPR, PF>::value : occ;
+    per_sm = occ > Tc16Occ<K, TPR, PFD>::value ? Tc16Occ<K, TPR, PFD>::value : occ;
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms * per_sm;
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16<K, TPR, PF><<<(int)grid, kTcThreads * TPR, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16<K, TPR, PFD><<<(int)grid, kTcThreads * TPR, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -678,11 +692,16 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     static thread_local TcStageParam sp;  // large: kept off the stack; the launch copies it
     if (stage_param(n, b, sp)) return b.k == 4 ? run_tc16s<4>(a, sp, dev_b, err, s) : run_tc16s<5>(a, sp, dev_b, err, s);
   }
-  if (!b.tc_prefetch && b.tc_rows == 1) {
-    if (b.k == 4) return run_tc16<4, 1, false>(a, n, b, dev_b, err, s);
-    if (b.k == 5) return run_tc16<5, 1, false>(a, n, b, dev_b, err, s);
+  if (b.tc_prefetch == 0 && b.tc_rows == 1) {
+    if (b.k == 4) return run_tc16<4, 1, 0>(a, n, b, dev_b, err, s);
+    if (b.k == 5) return run_tc16<5, 1, 0>(a, n, b, dev_b, err, s);
   }
-  if (!b.tc_prefetch && b.tc_rows == 2 && b.k == 6) return run_tc16<6, 2, false>(a, n, b, dev_b, err, s);
+  if (b.tc_prefetch == 0 && b.tc_rows == 2 && b.k == 6) return run_tc16<6, 2, 0>(a, n, b, dev_b, err, s);
+  if (b.tc_prefetch == 2 && b.tc_rows == 1) {
+    if (b.k == 4) return run_tc16<4, 1, 2>(a, n, b, dev_b, err, s);
+    if (b.k == 5) return run_tc16<5, 1, 2>(a, n, b, dev_b, err, s);
+  }
+  if (b.tc_prefetch == 2 && b.tc_rows == 2 && b.k == 6) return run_tc16<6, 2, 2>(a, n, b, dev_b, err, s);
   switch (b.k * 8 + b.tc_rows) {
     case 4 * 8 + 1: return run_tc16<4, 1>(a, n, b, dev_b, err, s);
     case 4 * 8 + 2: return run_tc16<4, 2>(a, n, b, dev_b, err, s);

@@ -123,14 +123,14 @@ def test_dense_block_every_target_class(dtype, k, tc):
         check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | tc, dtype)
 
 
-@pytest.mark.parametrize("rows,gather", [(1, 1), (1, 2), (2, 2), (4, 2), (1, 3), (2, 3)])
+@pytest.mark.parametrize("rows,gather", [(1, 1), (1, 2), (2, 2), (4, 2), (1, 3), (2, 3), (1, 4), (2, 4)])
 @pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n", [12, 17])
 def test_tc_threads_per_group(n, k, rows, gather):
     """The FP16 tensor-core kernel with one, two or four threads per group
     (row), with tiles staged through shared memory (gather 1, 4 and 5
-    targets) or gathered per thread with (gather 2) or without (gather 3)
-    the next tile in flight during the MMAs: high, low and bit-0 targets,
+    targets) or gathered per thread one tile ahead (gather 2), not ahead
+    (gather 3) or two tiles ahead (gather 4): high, low and bit-0 targets,
     a control outside the block, a partial last tile (n = 12) and many tiles
     (n = 17), from a random state."""
     rng = cg.SplitMix64(500 + 10 * k + n)
