@@ -1,8 +1,12 @@
-// Dense fused-block launches for complex64 states (FP32 accumulation).
+// Dense fused-block launches for complex64 states (FP32 accumulation),
+// 1..4 targets; 5 and 6 targets are in dense_c64_wide.cu (a translation unit
+// of their own, so the two compile in parallel).
 #include "kernels_common.cuh"
 
 namespace qs {
 namespace kern {
+
+cudaError_t run_dense_c64_wide(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads) {
   switch (b.k) {
@@ -10,8 +14,8 @@ cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat,
     case 2: return run_dense_param<float2, 2>(a, n, b, s, threads);
     case 3: return run_dense_param<float2, 3>(a, n, b, s, threads);
     case 4: return run_dense_param<float2, 4>(a, n, b, s, threads);
-    case 5: return run_dense_param<float2, 5>(a, n, b, s, threads);
-    case 6: return run_dense_smem<float2, 6>(a, n, b, (const float2 *)dev_mat, s, threads);
+    case 5:
+    case 6: return run_dense_c64_wide(a, n, b, dev_mat, s, threads);
     default: return cudaErrorInvalidValue;
   }
 }
