@@ -438,6 +438,16 @@ qs_status qs_batch_sync(qs_batch *b);   /* waits for the batch's stream */
 qs_status qs_batch_info(const qs_batch *b, qs_batch_info_t *out);
 void qs_batch_free(qs_batch *b);
 
+/*
+ * One-shot batch: qs_batch_create + one qs_batch_run + qs_batch_sync +
+ * qs_batch_free with the same arguments (NULL stream: the batch's own). Each
+ * state is set to |0...0> and its circuit applied in one persistent launch;
+ * returns after the results are in the states. For repeated runs keep the
+ * qs_batch handle instead (planning, upload and autotuning happen once).
+ */
+qs_status qs_apply_batch(qs_state *const *states, const qs_gate *const *gates, const size_t *n_gates, int count,
+                         uint64_t flags, const qs_opts *opts);
+
 const char *qs_last_error(void);
 
 #ifdef __cplusplus

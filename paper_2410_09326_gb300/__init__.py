@@ -164,6 +164,8 @@ def load(build_if_missing=False):
         "qs_batch_sync": (ctypes.c_int, [vp]),
         "qs_batch_info": (ctypes.c_int, [vp, ctypes.POINTER(qs_batch_info_t)]),
         "qs_batch_free": (None, [vp]),
+        "qs_apply_batch": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(sz),
+                                          ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(qs_opts)]),
         "qs_probs_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.c_int, vp, vp]),
         "qs_plan": (ctypes.c_int, [ctypes.c_int, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts),
@@ -411,6 +413,17 @@ def qs_batch_create(states, gate_arrays, flags=0, opts=None, stream=None):
                                _stream_handle(stream), ctypes.byref(h)))
     h._keep = arrs  # the library copies the gates; keep the arrays alive for the call only
     return h
+
+
+def qs_apply_batch(states, gate_arrays, flags=0, opts=None):
+    """One-shot batch: every state set to |0...0> and its circuit applied in
+    one persistent launch; returns when the results are in the states."""
+    count = len(states)
+    arrs = [np.ascontiguousarray(g, dtype=GATE_DTYPE) for g in gate_arrays]
+    st = (ctypes.c_void_p * count)(*[s.value for s in states])
+    gp = (ctypes.c_void_p * count)(*[a.ctypes.data for a in arrs])
+    ng = (ctypes.c_size_t * count)(*[a.size for a in arrs])
+    _check(load().qs_apply_batch(st, gp, ng, count, flags, ctypes.byref(opts) if opts is not None else None))
 
 
 def qs_batch_run(b):

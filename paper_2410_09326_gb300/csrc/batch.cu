@@ -454,4 +454,17 @@ void qs_batch_free(qs_batch *bt) {
   delete bt;
 }
 
+qs_status qs_apply_batch(qs_state *const *states, const qs_gate *const *gates, const size_t *n_gates, int count,
+                         uint64_t flags, const qs_opts *opts) {
+  qs_batch *bt = nullptr;
+  qs_status s = qs_batch_create(states, gates, n_gates, count, flags, opts, nullptr, &bt);
+  if (s != QS_OK) return s;
+  s = qs_batch_run(bt);
+  if (s == QS_OK) s = qs_batch_sync(bt);
+  const std::string err = s == QS_OK ? std::string() : qs::last_error_ref();
+  qs_batch_free(bt);
+  if (s != QS_OK) qs::last_error_ref() = err;
+  return s;
+}
+
 }  // extern "C"

@@ -77,3 +77,26 @@ def test_batch_rejects_bad_inputs():
         assert e.value.status == qs.QS_EINVAL
     finally:
         qs.qs_free_state(st)
+
+
+def test_one_shot_apply_batch():
+    """qs_apply_batch: create, one run, sync and free in one call; every state
+    ends at its own circuit's result from |0...0>."""
+    circuits = make_batch_inputs()[:10]
+    states = [qs.qs_alloc_state(n, qs.QS_C64) for n, _ in circuits]
+    try:
+        for (n, _), st in zip(circuits, states):
+            qs.qs_set_basis(st, 1)
+        qs.qs_apply_batch(states, [qs.gates_to_array(g) for _, g in circuits], qs.QS_VSWAP | qs.QS_DIAG)
+        for (n, gates), st in zip(circuits, states):
+            want, operm = oracle.simulate(cg.to_qasm(n, gates))
+            perm = qs.qs_get_perm(st, n)
+            assert list(perm) == list(operm)
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+            assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-5
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_apply_batch([states[0], states[0]], [qs.gates_to_array([("h", [0])])] * 2)
+        assert e.value.status == qs.QS_EINVAL
+    finally:
+        for st in states:
+            qs.qs_free_state(st)
