@@ -443,7 +443,8 @@ def run_case(args):
         gates = [g for g in cg.random_layered(n, 4, rng) if g[0] != "swap"]
         flags = qs.QS_TILE
     elif args.case == "permute":
-        gates = [("swap", [3, n - 2])]
+        pair = [int(x) for x in args.targets.split(",")] if args.targets else [3, n - 2]
+        gates = [("swap", pair)]
         flags = qs.QS_PLAIN
     else:
         gates = []

@@ -145,16 +145,39 @@ __global__ void __launch_bounds__(256) k_diag_chunk(T *__restrict__ a, const __g
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_permute(T *__restrict__ a, long long n_pairs, int qa, int qb) {
+// Exchange of physical bits qa < qb: the amplitudes with (bit qa, bit qb) =
+// (1, 0) and (0, 1) trade places. Each thread keeps kPermUnroll exchanges in
+// flight (all loads before the stores). With complex64 and qa >= 1 the two
+// amplitudes that differ only in bit 0 move together as one 16-byte access,
+// so bit 0 joins the fixed bits and every access is a full 16 bytes.
+constexpr int kPermUnroll = 4;
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_permute(V *__restrict__ a, long long n_items, int nf, int f0, int f1,
+                                                 int f2, unsigned long long da, unsigned long long db) {
+  const int fixed[3] = {f0, f1, f2};
   const long long stride = (long long)gridDim.x * blockDim.x;
-  const int fixed[2] = {qa, qb};
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n_pairs; j += stride) {
-    const uint64_t base = insert_zeros((uint64_t)j, fixed, 2);
-    const uint64_t i0 = base | (1ull << qa), i1 = base | (1ull << qb);
-    const T x = a[i0], y = a[i1];
-    a[i0] = y;
-    a[i1] = x;
+  long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; j + (kPermUnroll - 1) * stride < n_items; j += kPermUnroll * stride) {
+    V x[kPermUnroll], y[kPermUnroll];
+    uint64_t i0[kPermUnroll];
+#pragma unroll
+    for (int u = 0; u < kPermUnroll; u++) {
+      i0[u] = insert_zeros((uint64_t)(j + u * stride), fixed, nf);
+      x[u] = a[i0[u] + da];
+      y[u] = a[i0[u] + db];
+    }
+#pragma unroll
+    for (int u = 0; u < kPermUnroll; u++) {
+      a[i0[u] + da] = y[u];
+      a[i0[u] + db] = x[u];
+    }
+  }
+  for (; j < n_items; j += stride) {
+    const uint64_t i0 = insert_zeros((uint64_t)j, fixed, nf);
+    const V x = a[i0 + da], y = a[i0 + db];
+    a[i0 + da] = y;
+    a[i0 + db] = x;
   }
 }
 
@@ -275,7 +298,17 @@ __global__ void __launch_bounds__(256) k_probs_wide(const T *__restrict__ a, con
 template <typename T>
 cudaError_t run_block(T *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads) {
   if (b.kind == BK_PERMUTE) {
-    k_permute<T><<<grid_for(1ll << (n - 2), threads), threads, 0, s>>>(a, 1ll << (n - 2), b.q[0], b.q[1]);
+    const int qa = b.q[0], qb = b.q[1];  // qa < qb
+    if (sizeof(T) == 8 && qa >= 1) {
+      // 16-byte pairs over bit 0: indices in units of two amplitudes
+      const long long items = 1ll << (n - 3);
+      k_permute<float4><<<grid_for(items / kPermUnroll, threads), threads, 0, s>>>(
+          (float4 *)a, items, 2, qa - 1, qb - 1, 0, 1ull << (qa - 1), 1ull << (qb - 1));
+    } else {
+      const long long items = 1ll << (n - 2);
+      k_permute<T><<<grid_for(items / kPermUnroll, threads), threads, 0, s>>>(a, items, 2, qa, qb, 0, 1ull << qa,
+                                                                            1ull << qb);
+    }
     return cudaGetLastError();
   }
   if (b.kind == BK_DIAG) {
