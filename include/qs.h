@@ -126,7 +126,9 @@ typedef struct {
                            each choice is followed by this many gates of first-fit placement
                            and the one leaving the fewest blocks is taken; 0 = first fit
                            (qs_default_opts: 60) */
-  int reserved[3];
+  int no_shuffles;      /* 1: CUDA-core blocks whose targets cover bits 1, 2, 3 (bit 0 free) keep
+                           the thread-per-group kernel instead of warp-wide loads and shuffles (c64) */
+  int reserved[2];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

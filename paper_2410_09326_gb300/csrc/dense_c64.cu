@@ -9,6 +9,11 @@ namespace kern {
 cudaError_t run_dense_c64_wide(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads) {
+  if (b.k <= 3 && b.shuffles) {
+    bool used = false;
+    const cudaError_t e = run_dense_shfl_c64(a, n, b, s, used);
+    if (used || e != cudaSuccess) return e;
+  }
   switch (b.k) {
     case 1: return run_dense_param<float2, 1>(a, n, b, s, threads);
     case 2: return run_dense_param<float2, 2>(a, n, b, s, threads);

@@ -224,6 +224,10 @@ size_t phase_desc_bytes(const Block &b, bool c128);
 void phase_fill_desc(const Block &b, bool c128, void *out);
 cudaError_t run_phase(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s);
 
+// Warp-shuffle variant for 1..3 targets with one among bits 1..5 (dense_shfl.cu);
+// used = false when the block does not qualify (nothing launched).
+cudaError_t run_dense_shfl_c64(float2 *a, int n, const Block &b, cudaStream_t s, bool &used);
+
 cudaError_t run_dense_c64(float2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 cudaError_t run_dense_c128(double2 *a, int n, const Block &b, const void *dev_mat, cudaStream_t s, int threads);
 

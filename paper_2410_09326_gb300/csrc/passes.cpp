@@ -842,6 +842,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     if (b.tc_rows == 4 && b.k < 5) b.tc_rows = 2;  // a thread converts at least 4 amplitudes
     // staging tiles through shared memory measured slower than per-thread
     // gathers on GB300 (4.0 vs 6.3 TB/s at 5 targets), so it is opt-in
+    b.shuffles = opts.no_shuffles == 0;
     b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
     b.tc_prefetch = opts.tc_gather == 3 ? 0 : (opts.tc_gather == 4 ? 2 : 1);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;

@@ -62,6 +62,7 @@ struct Block {
   int tc_rows = 1;                // FP16 tensor-core kernel: threads per group (1 or 2)
   bool tc_staged = false;         // FP16 tensor-core kernel: tiles staged through shared memory
   int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
+  bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,

@@ -159,6 +159,36 @@ def test_tc_threads_per_group(n, k, rows, gather):
         assert np.linalg.norm(got - want) <= 1e-5
 
 
+@pytest.mark.parametrize("shuffles", [0, 1])
+@pytest.mark.parametrize("n", [9, 12, 16])
+def test_low_target_warp_shuffle_kernel(n, shuffles):
+    """3-target blocks on bits 1, 2, 3 (bit 0 free): the warp-shuffle kernel
+    (default) and the thread-per-group kernel (opts.no_shuffles = 1), with and
+    without a control above bit 5, from a random state."""
+    rng = cg.SplitMix64(900 + n)
+    o = qs.qs_default_opts()
+    o.no_shuffles = shuffles
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    for extra in ([], [("h", [n - 1]), ("ccx", [n - 1, 1, 3])]):
+        gates = []
+        for _ in range(2):
+            gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in (1, 2, 3)]
+            gates += [("cx", [1, 2]), ("cx", [3, 1])]
+        gates += extra
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(3), o)
+            _, recs = qs.qs_profile(st)
+            assert any(r.kind == 0 and r.k == 3 and [int(x) for x in r.qubits[:3]] == [1, 2, 3] for r in recs)
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5
+
+
 @pytest.mark.parametrize("n", [1, 2, 3])
 def test_tiny_registers(n):
     rng = cg.SplitMix64(77 + n)
