@@ -43,7 +43,7 @@ typedef enum {
   QS_EINVAL = 1,        /* bad argument (qubit out of range, duplicate, ...) */
   QS_ENOMEM = 2,        /* device or host allocation failed */
   QS_ECUDA = 3,         /* a CUDA call failed; the state is now invalid */
-  QS_EUNSUPPORTED = 4,  /* valid request this build does not handle */
+  QS_EUNSUPPORTED = 4,  /* valid request the library does not handle */
   QS_ETIMEOUT = 5,      /* a bounded device-side wait ran out */
   QS_ESTATE = 6         /* the state is invalid after an earlier CUDA error */
 } qs_status;
