@@ -48,7 +48,7 @@ except Exception:  # the binding constants need no library; keep import cheap
 
 
 def workload(n=N_QUBITS):
-    c = cg.config1_circuits(n=n)
+    c = cg.benchmark_circuits(n=n)
     _, ghz = c["ghz"]
     _, qft, _ = c["qft"]
     _, rnd = c["random"]
@@ -466,13 +466,13 @@ def run_case(args):
 
 
 def run_batch_bench(args):
-    """Config 3: 512 QAOA circuits (widths 10..20) in one persistent launch
+    """Batched workload: 512 QAOA circuits (widths 10..20) in one persistent launch
     replayed as a CUDA graph, against one launch per block per circuit.
     Prints its own JSON line (not the headline metric)."""
     import torch
     import paper_2410_09326_gb300 as qs
     qs.load(build_if_missing=True)
-    circuits = cg.config3_batch(count=args.batch)
+    circuits = cg.qaoa_batch(count=args.batch)
     stream = torch.cuda.Stream()
     states = [qs.qs_alloc_state(n, qs.QS_C64, stream=stream) for n, _ in circuits]
     arrays = [qs.gates_to_array(g) for _, g in circuits]
@@ -517,7 +517,7 @@ def run_batch_bench(args):
 
 
 def run_costmodel_bench(args):
-    """Config 4: train the MLP cost model on profiled blocks of seeded
+    """Cost-model workload: train the MLP cost model on profiled blocks of seeded
     circuits (n = 20..28), then choose flags for unseen n = 30 GHZ / QFT /
     random circuits; regret of each activator against brute force over the
     candidate flag sets (all measured on this GPU). Own JSON line."""
@@ -534,7 +534,7 @@ def run_costmodel_bench(args):
     loss = qs.qs_mlp_train(m, x, y, epochs=40, batch=256, lr=2e-3, seed=3)
     t_train = time.perf_counter() - t0
     n = N_QUBITS
-    c = cg.config1_circuits(n=n, index=9)
+    c = cg.benchmark_circuits(n=n, index=9)
     unseen = {"ghz": c["ghz"][1], "qft": c["qft"][1], "random": c["random"][1]}
     flat = qs.qs_class_table()
     for k in range(qs.QS_N_CLASSES):
@@ -573,7 +573,7 @@ def run_costmodel_bench(args):
 
 
 def run_tc32_bench(args):
-    """Config 2: n=32 complex64 (32 GiB), 40 layers of U3 + CX/CZ; fused k=4..6
+    """Tensor-core workload: n=32 complex64 (32 GiB), 40 layers of U3 + CX/CZ; fused k=4..6
     blocks on tensor cores against the FP32 CUDA-core kernels; the tensor-core
     result is compared with an FP64 (complex128, 64 GiB) GPU run of the same
     circuit. Own JSON line."""
@@ -581,7 +581,7 @@ def run_tc32_bench(args):
     import paper_2410_09326_gb300 as qs
     qs.load(build_if_missing=True)
     n = args.n if args.n != 26 else 32
-    _, gates = cg.config2_circuit(n=n, layers=40)
+    _, gates = cg.u3_entangler_circuit(n=n, layers=40)
     arr = qs.gates_to_array(gates)
     V = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_DIAG
     variants = {"tc_k4": V | qs.QS_FUSE_K(4) | qs.QS_TC, "tc_k5": V | qs.QS_FUSE_K(5) | qs.QS_TC,

@@ -66,9 +66,11 @@ class SplitMix64:
         return xs
 
 
-def seed_of(config_id, index):
-    """Seed rule for the stand-in workloads: config id x 1000 + circuit index."""
-    return config_id * 1000 + index
+def seed_of(family, index):
+    """Seed rule for the stand-in workloads: family id x 1000 + circuit index
+    (0 layered + SWAPs, 1 benchmark circuits, 2 U3 layers, 3 QAOA batch,
+    4 cost-model training)."""
+    return family * 1000 + index
 
 
 def fmt_gate(name, qubits, params=()):
@@ -199,13 +201,13 @@ def qaoa_maxcut(n, p, rng):
 # The five workload families
 # ---------------------------------------------------------------------------
 
-def config0_circuit(index=0, n=12, layers=20, n_swaps=10):
+def layered_swaps_circuit(index=0, n=12, layers=20, n_swaps=10):
     """Plain per-gate case: random 1q layers + CX matching + 10 random SWAPs."""
     rng = SplitMix64(seed_of(0, index))
     return n, random_layered(n, layers, rng, n_swaps=n_swaps)
 
 
-def config1_circuits(n=28, layers=30, index=0):
+def benchmark_circuits(n=28, layers=30, index=0):
     """GHZ, QFT of a random basis state with swaps, 30-layer random + 5% SWAP."""
     rng = SplitMix64(seed_of(1, index))
     q, x = qft(n, rng=rng)
@@ -216,13 +218,13 @@ def config1_circuits(n=28, layers=30, index=0):
     }
 
 
-def config2_circuit(n=32, layers=40, index=0):
+def u3_entangler_circuit(n=32, layers=40, index=0):
     """U3 layers (angles in [0, 2pi)) + CX/CZ (p = 1/2) on a random matching."""
     rng = SplitMix64(seed_of(2, index))
     return n, random_layered(n, layers, rng, one_q=("u3",), two_q=("cx", "cz"))
 
 
-def config3_batch(count=512, index=0, widths=(10, 12, 14, 16, 18, 20)):
+def qaoa_batch(count=512, index=0, widths=(10, 12, 14, 16, 18, 20)):
     """QAOA circuits of even width in [10, 20], p uniform in 1..4."""
     rng = SplitMix64(seed_of(3, index))
     out = []
@@ -234,8 +236,9 @@ def config3_batch(count=512, index=0, widths=(10, 12, 14, 16, 18, 20)):
     return out
 
 
-def config4_circuit(index, n_lo=20, n_hi=30, depth_lo=5, depth_hi=30):
-    """Cost-model training circuits: config-0-style layers, random n and depth."""
+def training_circuit(index, n_lo=20, n_hi=30, depth_lo=5, depth_hi=30):
+    """Cost-model training circuits: layered random circuits (random one-qubit
+    gates on every qubit, then CX on a random matching) of random n and depth."""
     rng = SplitMix64(seed_of(4, index))
     n = n_lo + rng.randint(n_hi - n_lo + 1)
     depth = depth_lo + rng.randint(depth_hi - depth_lo + 1)

@@ -62,7 +62,7 @@ def build_dataset(circuits, flag_sets=TRAIN_FLAGS, max_n=None):
 
 def training_circuits(count, n_lo=20, n_hi=30, index0=0):
     """Seeded training circuits of random width in [n_lo, n_hi]: mostly
-    config-4 layered random circuits, plus QFTs of random basis states, GHZ
+    layered random circuits, plus QFTs of random basis states, GHZ
     chains and QAOA ansaetze, so that wide diagonal blocks and chains are in
     the training distribution too."""
     out = []
@@ -71,7 +71,7 @@ def training_circuits(count, n_lo=20, n_hi=30, index0=0):
         rng = cg.SplitMix64(cg.seed_of(4, 100000 + index0 + i))
         n = n_lo + rng.randint(n_hi - n_lo + 1)
         if kind < 6:
-            out.append(cg.config4_circuit(index0 + i, n_lo=n_lo, n_hi=n_hi))
+            out.append(cg.training_circuit(index0 + i, n_lo=n_lo, n_hi=n_hi))
         elif kind < 8:
             gates, _ = cg.qft(n, rng=rng)
             out.append((n, gates))

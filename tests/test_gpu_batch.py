@@ -17,7 +17,7 @@ def lib():
 
 
 def make_batch_inputs():
-    circuits = cg.config3_batch(count=18, index=7)
+    circuits = cg.qaoa_batch(count=18, index=7)
     rng = cg.SplitMix64(4040)
     for n in (8, 13, 15, 17):  # random circuits with SWAPs: virtual swap inside the batch
         circuits.append((n, cg.random_layered(n, 6, rng, n_swaps=5)))

@@ -80,7 +80,7 @@ def test_learned_selection_gains_over_a_profile_free_model():
     try:
         qs.qs_mlp_train(m, x, y, epochs=40, batch=256, lr=2e-3, seed=2)
         n = 24
-        c = cg.config1_circuits(n=n, index=5)
+        c = cg.benchmark_circuits(n=n, index=5)
         unseen = {"ghz": c["ghz"][1], "qft": c["qft"][1], "random": c["random"][1]}
         flat = uniform_table()
         report = {}

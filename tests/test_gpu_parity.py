@@ -80,9 +80,9 @@ def check(n, gates, flags, dtype, init=None):
 
 @pytest.mark.parametrize("name", sorted(FLAGS))
 @pytest.mark.parametrize("index", [0, 1, 2])
-def test_config0_c128(name, index):
+def test_layered_swaps_n12_c128(name, index):
     """n=12 complex128 layered random circuit with 10 SWAPs."""
-    n, gates = cg.config0_circuit(index)
+    n, gates = cg.layered_swaps_circuit(index)
     check(n, gates, FLAGS[name], qs.QS_C128)
 
 
@@ -231,9 +231,9 @@ def test_qft_closed_form_n18(name, dtype):
     assert np.linalg.norm(got - want) < TOL[dtype]
 
 
-def test_config1_random_n20_vs_oracle():
+def test_benchmark_random_n20_vs_oracle():
     """The 30-layer random circuit with 5% SWAPs of the n=28 workload, at n=20."""
-    c = cg.config1_circuits(n=20)
+    c = cg.benchmark_circuits(n=20)
     n, gates = c["random"]
     for name in ("plain", "vswap", "vswap_k3_diag", "vswap_k5_diag", "vswap_k4_tc_diag", "vswap_k5_tc_diag"):
         check(n, gates, FLAGS[name], qs.QS_C64)
@@ -327,7 +327,7 @@ def test_measured_pgo_regret():
     flag sets on this GPU, picks a set whose measured time is within 15% of
     the best candidate's (brute force over the same candidates)."""
     n = 24
-    c = cg.config1_circuits(n=n)
+    c = cg.benchmark_circuits(n=n)
     _, gates = c["random"]
     arr = qs.gates_to_array(gates)
     st = qs.qs_alloc_state(n, qs.QS_C64)
@@ -495,7 +495,7 @@ def test_bench_size_n30_random_times_inverse():
     import bench
     from tests.test_oracle_pins import _inverse
     n = 30
-    c = cg.config1_circuits(n=n)
+    c = cg.benchmark_circuits(n=n)
     _, gates = c["random"]
     st = qs.qs_alloc_state(n, qs.QS_C64)
     try:

@@ -152,7 +152,7 @@ def test_tiles_with_fold_relocation_and_fusion_flags():
 def test_bench_size_n30_tiles_times_inverse():
     from tests.test_oracle_pins import _inverse
     n = 30
-    _, gates = cg.config1_circuits(n=n)["random"]
+    _, gates = cg.benchmark_circuits(n=n)["random"]
     st = qs.qs_alloc_state(n, qs.QS_C64)
     try:
         qs.qs_apply_circuit(st, qs.gates_to_array(gates), TILE)

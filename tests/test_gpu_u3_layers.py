@@ -21,15 +21,15 @@ def lib():
 
 
 @pytest.fixture(scope="module")
-def config2_n20():
-    n, gates = cg.config2_circuit(n=20, layers=40)
+def u3_layers_n20():
+    n, gates = cg.u3_entangler_circuit(n=20, layers=40)
     want, _ = oracle.simulate(cg.to_qasm(n, gates))
     return n, gates, want
 
 
 @pytest.mark.parametrize("name", sorted(VARIANTS))
-def test_config2_n20_vs_oracle(name, config2_n20):
-    n, gates, want = config2_n20
+def test_u3_layers_n20_vs_oracle(name, u3_layers_n20):
+    n, gates, want = u3_layers_n20
     st = qs.qs_alloc_state(n, qs.QS_C64)
     try:
         qs.qs_apply_circuit(st, qs.gates_to_array(gates), VARIANTS[name] | qs.QS_PROFILE)

@@ -153,20 +153,20 @@ def test_plan_reproduces_oracle_all_gate_types(flags):
 
 
 @pytest.mark.parametrize("flags", ALL_FLAGS[::3])
-def test_plan_reproduces_oracle_qft_and_config0(flags):
+def test_plan_reproduces_oracle_qft_and_layered_swaps(flags):
     n = 8
     gates, x = cg.qft(n, x=77)
     want, operm = oracle.simulate(cg.to_qasm(n, gates))
     got, perm, _ = plan_state(n, gates, flags)
     assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
-    n, gates = cg.config0_circuit(1)
+    n, gates = cg.layered_swaps_circuit(1)
     want, operm = oracle.simulate(cg.to_qasm(n, gates))
     got, perm, _ = plan_state(n, gates, flags)
     assert np.linalg.norm(got - oracle.to_physical(want, perm)) < 1e-12
 
 
 def test_fusion_reduces_blocks():
-    n, gates = cg.config0_circuit(0)
+    n, gates = cg.layered_swaps_circuit(0)
     arr = qs.gates_to_array(gates)
     counts = {k: len(qs.qs_plan(n, arr, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k))[0]) for k in range(1, 7)}
     plain = len(qs.qs_plan(n, arr, qs.QS_PLAIN)[0])
@@ -215,7 +215,7 @@ def test_plan_rejects_bad_gates():
 @pytest.mark.parametrize("flags", [qs.QS_PLAIN, qs.QS_VSWAP, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(3),
                                    qs.QS_FUSE | qs.QS_FUSE_K(2) | qs.QS_DIAG])
 def test_plan_perm_and_counts(flags):
-    n, gates = cg.config0_circuit(0)
+    n, gates = cg.layered_swaps_circuit(0)
     arr = qs.gates_to_array(gates)
     recs, mats, perm = qs.qs_plan(n, arr, flags)
     _, operm = oracle.simulate(cg.to_qasm(n, gates))
@@ -252,7 +252,7 @@ def test_swaps_absorbed_count():
 
 def test_rules_select_follows_the_paper_rules():
     # a SWAP present -> virtual swap; more than one gate -> fusion
-    n, gates = cg.config0_circuit(0)
+    n, gates = cg.layered_swaps_circuit(0)
     recs, _, perm = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_PGO_RULES)
     _, operm = oracle.simulate(cg.to_qasm(n, gates))
     assert list(perm) == list(operm)  # SWAPs were absorbed
@@ -260,7 +260,7 @@ def test_rules_select_follows_the_paper_rules():
 
 
 def test_measured_select_with_priors_prefers_wide_tensor_core_blocks():
-    c = cg.config1_circuits(n=30)
+    c = cg.benchmark_circuits(n=30)
     n, gates = c["random"]
     flags, ms = qs.qs_pgo_select(n, qs.gates_to_array(gates))
     assert flags & qs.QS_VSWAP and flags & qs.QS_FUSE and flags & qs.QS_TC
@@ -276,7 +276,7 @@ def test_measured_select_follows_the_table():
     """A table in which every tensor-core class ran slowly steers the choice
     away from the tensor cores; one in which wide CUDA-core blocks ran fast
     steers it to them."""
-    c = cg.config1_circuits(n=26)
+    c = cg.benchmark_circuits(n=26)
     n, gates = c["random"]
     arr = qs.gates_to_array(gates)
     t = qs.qs_class_table()
@@ -330,7 +330,7 @@ def test_relocation_moves_hot_low_bits_and_stays_exact(flags):
 
 
 def test_relocation_leaves_balanced_circuits_alone():
-    n, gates = cg.config0_circuit(0)
+    n, gates = cg.layered_swaps_circuit(0)
     recs, _, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_RELOCATE)
     assert not any(r.kind == 2 and r.n_gates == 0 for r in recs)
 
@@ -398,7 +398,7 @@ def test_tile_passes_cut_hbm_passes_at_n30():
     """At the benchmark width the tile planner needs far fewer passes over
     the state than 5-qubit fusion (the point of cache blocking) on circuits
     of dense gates."""
-    c = cg.config1_circuits(n=30)
+    c = cg.benchmark_circuits(n=30)
     fused = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG
     for name in ("ghz", "random"):
         arr = qs.gates_to_array(c[name][1])
@@ -460,7 +460,7 @@ def test_measured_select_picks_tile_passes_when_they_measured_fast():
     """Cache-blocked passes are a candidate of the measured-profile activator:
     chosen when the table says tile passes move bytes at HBM speed, not with
     the compiled-in priors (their CUDA-core arithmetic is the bound)."""
-    c = cg.config1_circuits(n=30)
+    c = cg.benchmark_circuits(n=30)
     n, gates = c["random"]
     arr = qs.gates_to_array(gates)
     flags, _ = qs.qs_pgo_select(n, arr)
@@ -479,7 +479,7 @@ def test_lookahead_fusion_never_adds_blocks_and_saves_them_on_layered_circuits()
     """The roll-out search keeps first fit's grouping unless it finds one with
     fewer blocks; on the layered random circuits it does (the measured step
     time follows the block count, each block being one HBM pass)."""
-    c = cg.config1_circuits(n=30)
+    c = cg.benchmark_circuits(n=30)
     arr = qs.gates_to_array(c["random"][1])
     first = qs.qs_default_opts()
     first.fuse_lookahead = 0

@@ -277,8 +277,8 @@ def test_circuit_times_inverse_is_identity(n):
 
 
 @pytest.mark.parametrize("index", range(3))
-def test_norm_preserved_config0(index):
-    n, gates = cg.config0_circuit(index)
+def test_norm_preserved_layered_swaps(index):
+    n, gates = cg.layered_swaps_circuit(index)
     psi, perm = oracle.simulate(cg.to_qasm(n, gates))
     assert abs(np.vdot(psi, psi).real - 1) < 1e-13
     assert sorted(perm) == list(range(n))
