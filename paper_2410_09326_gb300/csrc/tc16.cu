@@ -309,10 +309,10 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
 // K targets (the other bits fixed per tile). Bits 0..6 always lie in it, so
 // in address order the tile is made of contiguous runs of at least 1 KiB,
 // whatever the targets: the CTA copies it into shared memory with 16-byte
-// cp.async in address order (the next tile's copies fly during the MMAs and
-// the epilogue), each thread then reads its group's row from a layout in
-// which consecutive rows are consecutive words, and the results leave the
-// same way through the (by then idle) A buffers. Element e of the tile (its
+// cp.async in address order, two tiles ahead (two staging buffers, so two
+// tiles' loads are in flight per CTA without holding registers), each thread
+// then reads its group's row from a layout in which consecutive rows are
+// consecutive words, and stores its results directly. Element e of the tile (its
 // local index, bit j = j-th lowest bit of the sub-cube) sits at global offset
 // dep_lo[e & 63] + dep_hi[e >> 6] from the tile base and at staging slot
 // slot_lo[e & 63] + slot_hi[e >> 6], slot(r, s) = 128 s + r, or
@@ -324,6 +324,8 @@ struct TcStageParam {
   int hi_pos[40];
   int pair;                       // bit 0 is target 0
   int withhold_commit;
+  int low7[7];                    // the 7 lowest free bits (row r's bits, in order)
+  int tq[QS_MAX_FUSE];            // targets ascending (matrix bit order)
   unsigned long long dep_lo[64], dep_hi[64];
   unsigned short slot_lo[64], slot_hi[64];
 };
@@ -346,28 +348,25 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   constexpr uint32_t LBO = 128u;
   constexpr uint32_t NCOLS = 2 * KR;
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
-  static_assert(2 * A_BYTES == ELEMS * 8u, "the A buffers hold one tile of outputs");
+  constexpr uint32_t IN_BYTES = (uint32_t)ELEMS * 8u;
 
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *sA_hi = smem;
   unsigned char *sA_lo = smem + A_BYTES;
-  float2 *sOut = reinterpret_cast<float2 *>(smem);            // A buffers, reused for the outputs
   unsigned char *sB = smem + 2 * A_BYTES;                     // hi then lo
-  float2 *sIn = reinterpret_cast<float2 *>(smem + 2 * A_BYTES + 2 * B_BYTES);
+  float2 *sIn0 = reinterpret_cast<float2 *>(smem + 2 * A_BYTES + 2 * B_BYTES);  // two staging buffers
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
-  __shared__ unsigned long long dep_lo[64], dep_hi[64];
-  __shared__ unsigned short slot_lo[64], slot_hi[64];
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
-  if (tid < 64) {
-    dep_lo[tid] = p.dep_lo[tid];
-    dep_hi[tid] = p.dep_hi[tid];
-    slot_lo[tid] = p.slot_lo[tid];
-    slot_hi[tid] = p.slot_hi[tid];
-  }
+  // the copies of thread tid are the elements e = 2 tid + 256 j: their low
+  // 6 bits are the thread's own, their high bits (tid / 32 + 4 j) are the
+  // same across a warp, so the high tables are read from the parameter bank
+  // as broadcasts and shared memory stays free for the two staging buffers
+  const unsigned long long my_dep = p.dep_lo[(2 * tid) & 63];
+  const uint32_t my_slot = p.slot_lo[(2 * tid) & 63];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                  "r"(NCOLS));
@@ -384,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const uint32_t mbar_a = smem_addr(&mbar);
   const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
   const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
-  const uint32_t in_addr = smem_addr(sIn);
+  const uint32_t in_addr0 = smem_addr(sIn0);
   const int r = tid;
   const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
   const bool pair = p.pair != 0;
@@ -394,24 +393,46 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     for (int j = 0; j < p.nhi; j++) b |= (uint64_t)((t >> j) & 1) << p.hi_pos[j];
     return b;
   };
-  auto issue_loads = [&](long long t) {
-    const uint64_t tb = tile_base(t);
+  // one commit group per tile slot, empty past the last tile, so that
+  // "all but the newest group" always means "the tile about to be used"
+  auto issue_loads = [&](long long t, int buf) {
+    if (t < p.n_tiles) {
+      const uint64_t tb = tile_base(t);
+      const uint32_t dst = in_addr0 + (uint32_t)buf * IN_BYTES;
 #pragma unroll 4
-    for (int e = 2 * tid; e < ELEMS; e += 2 * kTcThreads) {
-      const uint64_t off = tb + dep_lo[e & 63] + dep_hi[e >> 6];
-      const uint32_t slot = (uint32_t)slot_lo[e & 63] + slot_hi[e >> 6];
-      cp_async16(in_addr + slot * 8u, a + off);
+      for (int e = 2 * tid; e < ELEMS; e += 2 * kTcThreads) {
+        const uint64_t off = tb + my_dep + p.dep_hi[e >> 6];
+        const uint32_t slot = my_slot + p.slot_hi[e >> 6];
+        cp_async16(dst + slot * 8u, a + off);
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // this thread's group base within a tile, and target offsets
+  uint64_t rbase = 0;
+#pragma unroll
+  for (int j = 0; j < 7; j++) rbase |= (uint64_t)((r >> j) & 1) << p.low7[j];
+  uint64_t d[K];
+#pragma unroll
+  for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
+  auto offset = [&](int s) {
+    uint64_t off = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++)
+      if ((s >> j) & 1) off += d[j];
+    return off;
   };
 
   uint32_t phase = 0;
   bool aborted = false;
   long long tile = blockIdx.x;
-  if (tile < p.n_tiles) issue_loads(tile);
-  for (; tile < p.n_tiles; tile += gridDim.x) {
-    asm volatile("cp.async.wait_all;" ::: "memory");
+  issue_loads(tile, 0);
+  issue_loads(tile + gridDim.x, 1);
+  int buf = 0;
+  for (; tile < p.n_tiles; tile += gridDim.x, buf ^= 1) {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
+    const float2 *sIn = sIn0 + (size_t)buf * ELEMS;
     // this thread's group (row r) out of the staged tile
     float2 v[D];
     if (pair) {
@@ -472,9 +493,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
       if (!p.withhold_commit) mma_commit(mbar_a);
     }
-    // every row has been read out of the staging buffer: refill it
-    const uint64_t cur_base = tile_base(tile);
-    if (tile + gridDim.x < p.n_tiles) issue_loads(tile + gridDim.x);
+    // every row has been read out of this staging buffer: refill it with
+    // the tile after next
+    const uint64_t cur_base = tile_base(tile) + rbase;
+    issue_loads(tile + 2 * (long long)gridDim.x, buf);
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -498,30 +520,30 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
     }
     const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
-    // outputs into the A buffers (the MMAs that read them have completed)
+    // scale and store, 8 amplitudes per chunk
 #pragma unroll
     for (int h = 0; h < KR / 16; h++) {
       uint32_t rb[16], rs[16];
       TmemLd<16>::run(lane_base + 16 * h, rb);
       TmemLd<16>::run(lane_base + KR + 16 * h, rs);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (pair) {
 #pragma unroll
-      for (int u = 0; u < 8; u++) {
-        const int s = 8 * h + u;
-        const float2 y = make_float2((__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
-                                     (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
-        if (pair) sOut[(s >> 1) * 256 + 2 * r + (s & 1)] = y;
-        else sOut[s * 128 + r] = y;
+        for (int u = 0; u < 4; u++) {
+          const int sl = 8 * h + 2 * u;
+          float y[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) y[q] = (__uint_as_float(rb[4 * u + q]) + __uint_as_float(rs[4 * u + q])) * f;
+          *reinterpret_cast<float4 *>(a + cur_base + offset(sl)) = make_float4(y[0], y[1], y[2], y[3]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          a[cur_base + offset(8 * h + u)] =
+              make_float2((__uint_as_float(rb[2 * u]) + __uint_as_float(rs[2 * u])) * f,
+                          (__uint_as_float(rb[2 * u + 1]) + __uint_as_float(rs[2 * u + 1])) * f);
       }
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int e = 2 * tid; e < ELEMS; e += 2 * kTcThreads) {
-      const uint64_t off = cur_base + dep_lo[e & 63] + dep_hi[e >> 6];
-      const uint32_t slot = (uint32_t)slot_lo[e & 63] + slot_hi[e >> 6];
-      *reinterpret_cast<float4 *>(a + off) = *reinterpret_cast<const float4 *>(sOut + slot);
-    }
-    // the next iteration's barrier orders these reads before A is rewritten
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -586,6 +608,8 @@ bool stage_param(int n, const Block &b, TcStageParam &p) {
     p.slot_lo[x] = (unsigned short)sl;
     p.slot_hi[x] = (unsigned short)sh;
   }
+  for (int j = 0; j < 7; j++) p.low7[j] = freep[j];
+  for (int j = 0; j < b.k; j++) p.tq[j] = b.q[j];
   p.nhi = 0;
   for (int j = 7; j < nfree; j++) p.hi_pos[p.nhi++] = freep[j];
   p.n_tiles = 1ll << p.nhi;
@@ -596,7 +620,7 @@ bool stage_param(int n, const Block &b, TcStageParam &p) {
 
 template <int K> size_t tc16s_smem_bytes() {
   constexpr size_t KR = 2 << K;
-  return 2 * 128 * KR * 2 + 2 * KR * KR * 2 + (size_t)128 * (1 << K) * 8;
+  return 2 * 128 * KR * 2 + 2 * KR * KR * 2 + 2 * (size_t)128 * (1 << K) * 8;
 }
 
 template <int K>
