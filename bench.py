@@ -617,6 +617,76 @@ def run_tc32_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation_bench(args):
+    """Pass-by-pass ablation on the benchmark circuits (n = 28 by default):
+    plain per-gate kernels, virtual swap alone, virtual swap + fusion of
+    width k = 2..6 (diagonal runs fused, tensor cores for k >= 4), the rule
+    activator, and the measured-profile activator after profiled calibration
+    runs; plus the QFT with and without virtual swap at n = 20..32, the GPU
+    counterpart of the paper's virtual-swap table (Sec. IV-C). Device time of
+    the planned blocks (CUDA events), best of 3. Own JSON line."""
+    import torch
+    import paper_2410_09326_gb300 as qs
+    qs.load(build_if_missing=True)
+    n = args.n if args.n != 26 else 28
+
+    def best_ms(st, gates, flags, reps=3):
+        best = float("inf")
+        for _ in range(reps):
+            qs.qs_set_basis(st, 0)
+            qs.qs_apply_circuit(st, gates, flags | qs.QS_PROFILE)
+            summ, _ = qs.qs_profile(st, with_records=False)
+            best = min(best, summ.total_ms)
+        return best, summ.n_blocks
+
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    c = cg.benchmark_circuits(n=n)
+    named = {"ghz": c["ghz"][1], "qft": c["qft"][1], "random": c["random"][1]}
+    variants = {"plain": qs.QS_PLAIN, "vswap": qs.QS_VSWAP}
+    for k in range(2, 7):
+        variants[f"vswap_k{k}"] = qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | (qs.QS_TC if k >= 4 else 0)
+    variants["rules"] = qs.QS_PGO_RULES
+    out = {}
+    for name, gates in named.items():
+        arr = qs.gates_to_array(gates)
+        res = {}
+        for v, f in variants.items():
+            ms, nb = best_ms(st, arr, f, reps=1 if v == "plain" else 3)
+            res[v] = {"ms": round(ms, 2), "launches": nb}
+        out[name] = res
+    # measured-profile activator: profiled calibration runs, then one choice per circuit
+    for f in CALIBRATION_FLAGS(qs):
+        for gates in named.values():
+            qs.qs_set_basis(st, 0)
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), f | qs.QS_PROFILE)
+            qs.qs_profile(st, with_records=False)
+    table = qs.qs_profile_classes(st)
+    for name, gates in named.items():
+        arr = qs.gates_to_array(gates)
+        f, _ = qs.qs_pgo_select(n, arr, table=table)
+        ms, nb = best_ms(st, arr, f)
+        out[name]["pgo_measured"] = {"ms": round(ms, 2), "launches": nb, "flags": hex(f)}
+        for v in list(out[name]):
+            out[name][v]["speedup_vs_plain"] = round(out[name]["plain"]["ms"] / out[name][v]["ms"], 2)
+    qs.qs_free_state(st)
+    qft = {}
+    for m in range(20, min(32, args.qft_max) + 1, 2):
+        s2 = qs.qs_alloc_state(m, qs.QS_C64)
+        gates, _ = cg.qft(m, rng=cg.SplitMix64(cg.seed_of(1, m)))
+        arr = qs.gates_to_array(gates)
+        plain, _ = best_ms(s2, arr, qs.QS_PLAIN, reps=1 if m >= 30 else 3)
+        vs, _ = best_ms(s2, arr, qs.QS_VSWAP, reps=1 if m >= 30 else 3)
+        qs.qs_free_state(s2)
+        qft[m] = {"plain_ms": round(plain, 2), "vswap_ms": round(vs, 2), "speedup": round(plain / vs, 3)}
+    torch.cuda.synchronize()
+    line = {"config": "ablation", "workload": f"n={n} c64 benchmark circuits (GHZ, QFT with swap network, 30-layer "
+                                             "random with 5% SWAP); QFT n=20..32 with/without virtual swap",
+            "circuits": out, "qft_virtual_swap": qft,
+            "note": "device time of the planned blocks (CUDA events), best of 3 (plain: 1); "
+                    "paper (CPU/SSD, context only): virtual swap 1.19x average, QFT 1.01-1.13x"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -632,10 +702,11 @@ def main():
     ap.add_argument("--tc-gather", type=int, default=0, help="tensor-core tiles: 1 staged, 2 per-thread gathers (--case)")
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
     ap.add_argument("--tc-precision", type=int, default=0, help="tensor-core operands: 0 two FP16 halves, 1 3xTF32")
-    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32"],
+    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32", "ablation"],
                     help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
     ap.add_argument("--train-circuits", type=int, default=60)
     ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--qft-max", type=int, default=32, help="ablation: widest QFT of the virtual-swap table")
     args = ap.parse_args()
     if args.case:
         run_case(args)
@@ -648,6 +719,9 @@ def main():
         return
     if args.config == "tc32":
         run_tc32_bench(args)
+        return
+    if args.config == "ablation":
+        run_ablation_bench(args)
         return
     if args.warmup < 3:
         args.warmup = 3
