@@ -660,6 +660,28 @@ def run_ablation_bench(args):
             qs.qs_set_basis(st, 0)
             qs.qs_apply_circuit(st, qs.gates_to_array(gates), f | qs.QS_PROFILE)
             qs.qs_profile(st, with_records=False)
+    # cost of the context profile (a CUDA event pair per block, Sec. III-C):
+    # the same rule-activated runs timed around the whole call, with and
+    # without QS_PROFILE (the gate counters are always kept)
+    overhead = {}
+    for name, gates in named.items():
+        arr = qs.gates_to_array(gates)
+        times = {}
+        for label, extra in (("off", 0), ("on", qs.QS_PROFILE)):
+            best = float("inf")
+            for _ in range(5):
+                qs.qs_set_basis(st, 0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                qs.qs_apply_circuit(st, arr, qs.QS_PGO_RULES | extra)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            times[label] = best
+        overhead[name] = {"ms_without": round(times["off"], 2), "ms_with": round(times["on"], 2),
+                          "overhead_pct": round(100 * (times["on"] / times["off"] - 1), 2)}
     table = qs.qs_profile_classes(st)
     for name, gates in named.items():
         arr = qs.gates_to_array(gates)
@@ -681,7 +703,7 @@ def run_ablation_bench(args):
     torch.cuda.synchronize()
     line = {"config": "ablation", "workload": f"n={n} c64 benchmark circuits (GHZ, QFT with swap network, 30-layer "
                                              "random with 5% SWAP); QFT n=20..32 with/without virtual swap",
-            "circuits": out, "qft_virtual_swap": qft,
+            "circuits": out, "qft_virtual_swap": qft, "context_profile_overhead": overhead,
             "note": "device time of the planned blocks (CUDA events), best of 3 (plain: 1); "
                     "paper (CPU/SSD, context only): virtual swap 1.19x average, QFT 1.01-1.13x"}
     print(json.dumps(line), flush=True)
