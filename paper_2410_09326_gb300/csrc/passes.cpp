@@ -157,7 +157,7 @@ void greedy_groups(const std::vector<qs_gate> &pg, const std::vector<int> &idx, 
 // limit(all_diag_block_and_gate) is the width bound.
 template <typename Limit>
 void lookahead_groups(const std::vector<qs_gate> &pg, const std::vector<int> &idx, std::vector<Pending> &groups,
-                      Limit limit, int horizon) {
+                      Limit limit, int horizon, int tail_blocks = 6) {
   struct LG {
     uint64_t qmask;
     bool all_diag;
@@ -226,7 +226,8 @@ void lookahead_groups(const std::vector<qs_gate> &pg, const std::vector<int> &id
           place(G2, la2, ln2, y, b);
         }
         long tail = 0;
-        for (int b = std::max(0, (int)G2.size() - 6); b < (int)G2.size(); b++) tail += popcount64(G2[b].qmask);
+        for (int b = std::max(0, (int)G2.size() - tail_blocks); b < (int)G2.size(); b++)
+          tail += popcount64(G2[b].qmask);
         if (best_blocks < 0 || (long)G2.size() < best_blocks ||
             ((long)G2.size() == best_blocks && tail < best_tail)) {
           best_blocks = (long)G2.size();
@@ -797,21 +798,25 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     auto limit = [&](bool nd) { return nd ? (dfuse ? dlimit : std::max(K, 1)) : K; };
     if (opts.fuse_lookahead > 0) {
       // the roll-out heuristic usually saves blocks but is not guaranteed
-      // to, and its best horizon varies: plain first fit and roll-outs of
-      // L and 4L/3 gates run side by side, the grouping with the fewest
-      // blocks is launched (earliest of them on a tie)
-      std::vector<Pending> alt[3];
-      const int horizons[3] = {0, opts.fuse_lookahead, opts.fuse_lookahead + opts.fuse_lookahead / 3};
-      run_tasks(3, [&](size_t v) {
+      // to, and its best horizon and tie-break vary: plain first fit and
+      // roll-outs of L, 4L/3 and 5L/3 gates (ties broken by the width of the
+      // last 6 or 12 blocks) run side by side on host threads, and the
+      // grouping with the fewest blocks is launched (earliest on a tie)
+      constexpr int kVariants = 6;
+      std::vector<Pending> alt[kVariants];
+      const int L = opts.fuse_lookahead;
+      const int horizons[kVariants] = {0, L, L, L + L / 3, L + L / 3, L + 2 * L / 3};
+      const int tails[kVariants] = {0, 6, 12, 6, 12, 6};
+      run_tasks(kVariants, [&](size_t v) {
         if (v == 0)
           greedy_groups(pg, all, alt[0], [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
             return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
           });
         else
-          lookahead_groups(pg, all, alt[v], limit, horizons[v]);
+          lookahead_groups(pg, all, alt[v], limit, horizons[v], tails[v]);
       });
       int best = 0;
-      for (int v = 1; v < 3; v++)
+      for (int v = 1; v < kVariants; v++)
         if (alt[v].size() < alt[best].size()) best = v;
       groups.swap(alt[best]);
     } else {
