@@ -421,6 +421,7 @@ def run_case(args):
     opts.tc_precision = args.tc_precision
     opts.tc_row_threads = args.tc_rows
     opts.tc_gather = args.tc_gather
+    opts.tc_split_k = args.tc_split_k
     if k:
         qubits = [1, 6, 11, 16, 21, 24][:k] if n > 24 else list(range(0, 2 * k, 2))
         if args.targets:
@@ -722,6 +723,7 @@ def main():
     ap.add_argument("--launches", type=int, default=3)
     ap.add_argument("--tc-rows", type=int, default=0, help="threads per group of the FP16 tensor-core kernel (--case)")
     ap.add_argument("--tc-gather", type=int, default=0, help="tensor-core tiles: 1 staged, 2 per-thread gathers (--case)")
+    ap.add_argument("--tc-split-k", type=int, default=0, help="6-target tensor-core blocks: 1 split K, 2 whole K (--case)")
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
     ap.add_argument("--tc-precision", type=int, default=0, help="tensor-core operands: 0 two FP16 halves, 1 3xTF32")
     ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32", "ablation"],

@@ -128,7 +128,9 @@ typedef struct {
                            (qs_default_opts: 60) */
   int no_shuffles;      /* 1: CUDA-core blocks whose targets cover bits 1, 2, 3 (bit 0 free) keep
                            the thread-per-group kernel instead of warp-wide loads and shuffles (c64) */
-  int reserved[2];
+  int tc_split_k;       /* 6-target tensor-core blocks: 1 = K in two halves through 96 KB of shared
+                           memory (two CTAs per SM), 2 = whole K (128 KB, one CTA); 0 = default */
+  int reserved[1];
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

@@ -674,6 +674,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     return QS_EUNSUPPORTED;
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
+  if (opts.tc_split_k < 0 || opts.tc_split_k > 2) {
+    err = "opts.tc_split_k out of range (0..2)";
+    return QS_EINVAL;
+  }
   if (opts.tc_gather < 0 || opts.tc_gather > 4) {
     err = "opts.tc_gather out of range (0..4)";
     return QS_EINVAL;
@@ -848,6 +852,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     // staging tiles through shared memory measured slower than per-thread
     // gathers on GB300 (4.0 vs 6.3 TB/s at 5 targets), so it is opt-in
     b.shuffles = opts.no_shuffles == 0;
+    b.tc_splitk = b.tc && b.k == 6 && b.tc_rows == 2 && opts.tc_split_k == 1;
     b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
     b.tc_prefetch = opts.tc_gather == 3 ? 0 : (opts.tc_gather == 4 ? 2 : 1);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;

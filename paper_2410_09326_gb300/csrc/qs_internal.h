@@ -63,6 +63,7 @@ struct Block {
   bool tc_staged = false;         // FP16 tensor-core kernel: tiles staged through shared memory
   int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
+  bool tc_splitk = false;         // 6-target tensor-core blocks: K in two halves (two CTAs per SM)
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,

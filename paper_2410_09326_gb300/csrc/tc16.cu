@@ -56,9 +56,9 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 // prefetch a thread needs fewer registers, so more CTAs fit and they hide
 // each other's gathers; two tiles ahead keep loads in flight across a whole
 // tile at the price of registers.
-template <int K, int TPR, int PFD = 1> struct Tc16Occ {
+template <int K, int TPR, int PFD = 1, bool SK = false> struct Tc16Occ {
   static constexpr int value =
-      TPR == 4 ? 1
+      SK ? 2 : TPR == 4 ? 1
                : (PFD == 1 ? (K <= 4 ? 4 : (K == 5 ? 3 : 1))
                            : (PFD == 0 ? (K <= 4 ? 6 : (K == 5 ? 4 : 1)) : (K <= 4 ? 3 : (K == 5 ? 2 : 1))));
 };
@@ -69,21 +69,28 @@ template <int K, int TPR, int PFD = 1> struct Tc16Occ {
 // (warps w and w + 4 see the same lane quadrant). The row's scale and norms
 // are combined through shared memory. More threads per row means fewer
 // registers per thread and more warps per SM to hide the gather latency.
-template <int K, int TPR, int PFD>
-__global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
+// SK (split K, with TPR = 2): the A buffers hold one half of the K columns at
+// a time -- thread half h is exactly K half h -- so the MMAs run in two
+// rounds (half 0, wait, half 1) and the shared memory of 6-target blocks
+// drops from 128 KB to 96 KB: two CTAs fit per SM.
+template <int K, int TPR, int PFD, bool SK = false>
+__global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::value)
     k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
                  int *__restrict__ err) {
   constexpr int NT = kTcThreads * TPR;
   constexpr int D = 1 << K;                    // amplitudes per group
   constexpr int DH = D / TPR;                  // amplitudes per thread
   constexpr int KR = 2 * D;                    // real K = N of the GEMM
-  constexpr uint32_t A_BYTES = 128u * KR * 2u;
+  constexpr int KA = SK ? KR / 2 : KR;         // K columns held in the A buffers
+  constexpr uint32_t A_BYTES = 128u * KA * 2u;
   constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
-  constexpr uint32_t SBO = (KR / 8) * 128u;    // 8-row groups (both operands)
+  constexpr uint32_t SBO = (KR / 8) * 128u;    // 8-row groups of B
+  constexpr uint32_t SBO_A = (KA / 8) * 128u;  // 8-row groups of A
   constexpr uint32_t LBO = 128u;               // K-adjacent core matrices
   constexpr uint32_t NCOLS = 2 * KR;           // large and small accumulators
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
   static_assert(DH % 4 == 0, "a thread converts whole 16-byte core-matrix rows");
+  static_assert(!SK || TPR == 2, "split K pairs each thread half with a K half");
 
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *sA_hi = smem;
@@ -123,7 +130,7 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
   for (int j = 0; j < K; j++) d[j] = 1ull << p.tq[j];
   const bool pair = p.tq[0] == 0;
   // this thread's row of A: 8-row group (r / 8), row (r % 8) of each core matrix
-  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+  const uint32_t row_off = (uint32_t)(r >> 3) * SBO_A + (uint32_t)(r & 7) * 16u;
   uint32_t phase = 0;
   bool aborted = false;
 
@@ -182,9 +189,10 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
     if (mx > 0.f) frexpf(mx, &e);
     const float sc = ldexpf(1.f, -e);
     // hi/lo rows: amplitudes 4c..4c+3 fill the 16-byte row of core matrix c
+    auto convert = [&]() {
 #pragma unroll
     for (int cl = 0; cl < DH / 4; cl++) {
-      const int c = s0 / 4 + cl;
+      const int c = SK ? cl : s0 / 4 + cl;
       float x[8];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
@@ -203,23 +211,54 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD>::value)
       *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
       *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
+    };
+    // MMAs over K steps [k0, k0 + nks) of 16 columns; A holds them from step 0
+    auto issue = [&](int k0, int nks) {
+      if (tid == 0) {
 #pragma unroll
-      for (int ks = 0; ks < KR / 16; ks++) {
-        const uint32_t koff = (uint32_t)ks * 2u * LBO;
-        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
-        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
-        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
-        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
-        mma_f16(tmem, dah, dbh, IDESC, ks > 0 ? 1u : 0u);
-        mma_f16(tmem + KR, dah, dbl, IDESC, ks > 0 ? 1u : 0u);
-        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+        for (int ks = 0; ks < KA / 16; ks++) {
+          if (ks >= nks) break;
+          const uint32_t aoff = (uint32_t)ks * 2u * LBO;
+          const uint32_t boff = (uint32_t)(k0 + ks) * 2u * LBO;
+          const uint64_t dah = make_desc(a_hi + aoff, LBO, SBO_A);
+          const uint64_t dal = make_desc(a_lo + aoff, LBO, SBO_A);
+          const uint64_t dbh = make_desc(b_hi + boff, LBO, SBO);
+          const uint64_t dbl = make_desc(b_lo + boff, LBO, SBO);
+          const uint32_t acc = (k0 + ks) > 0 ? 1u : 0u;
+          mma_f16(tmem, dah, dbh, IDESC, acc);
+          mma_f16(tmem + KR, dah, dbl, IDESC, acc);
+          mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+        }
+        if (!p.withhold_commit) mma_commit(mbar_a);
       }
-      if (!p.withhold_commit) mma_commit(mbar_a);
+    };
+    auto publish = [&]() {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+    };
+    if constexpr (SK) {
+      // K half 0 from thread half 0; its MMAs must finish reading A before
+      // thread half 1 overwrites it with K half 1
+      if (h == 0) convert();
+      publish();
+      issue(0, KR / 32);
+      const bool ok0 = mbar_wait(mbar_a, phase);
+      phase ^= 1;
+      if (!__syncthreads_and(ok0)) {
+        if (tid == 0) atomicExch(err, 1);
+        aborted = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (h == 1) convert();
+      publish();
+      issue(KR / 32, KR / 32);
+    } else {
+      convert();
+      publish();
+      issue(0, KR / 16);
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
@@ -650,7 +689,7 @@ template <int K> size_t tc16_smem_bytes() {
   return 2 * 128 * KR * 2 + 2 * KR * KR * 2;
 }
 
-template <int K, int TPR, int PFD = 1>
+template <int K, int TPR, int PFD = 1, bool SK = false>
 cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
   TcParam p;
   p.n_groups = 1ll << (n - K - b.nctrl);
@@ -659,7 +698,7 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   p.withhold_commit = b.withhold_commit ? 1 : 0;
   fill_fixed(b, p.fixed, p.nf);
   for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
-  const size_t smem = tc16_smem_bytes<K>();
+  const size_t smem = SK ? tc16_smem_bytes<K>() - (size_t)128 * (2 << K) * 2 : tc16_smem_bytes<K>();
   // per device: opt in to the shared memory and size one wave of resident
   // CTAs; TMEM columns stay within 512 per SM (4 x 64, 3 x 128, 1 x 256)
   static thread_local int configured = -1;
@@ -668,18 +707,18 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   cudaGetDevice(&dev);
   if (configured != dev) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_dense_tc16<K, TPR, PFD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dense_tc16<K, TPR, PFD, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16<K, TPR, PFD>, kTcThreads * TPR, smem);
+    const int occ = resident_ctas((const void *)k_dense_tc16<K, TPR, PFD, SK>, kTcThreads * TPR, smem);
     // TMEM: at most 512 columns per SM (2 x KR columns per CTA)
     const int tmem_cap = 512 / (4 << K);
-    per_sm = occ > Tc16Occ<K, TPR, PFD>::value ? Tc16Occ<K, TPR, PFD>::value : occ;
+    per_sm = occ > Tc16Occ<K, TPR, PFD, SK>::value ? Tc16Occ<K, TPR, PFD, SK>::value : occ;
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms * per_sm;
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16<K, TPR, PFD><<<(int)grid, kTcThreads * TPR, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16<K, TPR, PFD, SK><<<(int)grid, kTcThreads * TPR, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -726,6 +765,7 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     if (b.k == 5) return run_tc16<5, 1, 2>(a, n, b, dev_b, err, s);
   }
   if (b.tc_prefetch == 2 && b.tc_rows == 2 && b.k == 6) return run_tc16<6, 2, 2>(a, n, b, dev_b, err, s);
+  if (b.tc_splitk && b.tc_rows == 2 && b.k == 6) return run_tc16<6, 2, 1, true>(a, n, b, dev_b, err, s);
   switch (b.k * 8 + b.tc_rows) {
     case 4 * 8 + 1: return run_tc16<4, 1>(a, n, b, dev_b, err, s);
     case 4 * 8 + 2: return run_tc16<4, 2>(a, n, b, dev_b, err, s);

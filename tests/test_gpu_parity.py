@@ -123,10 +123,11 @@ def test_dense_block_every_target_class(dtype, k, tc):
         check(n, gates + gates2, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | tc, dtype)
 
 
-@pytest.mark.parametrize("rows,gather", [(1, 1), (1, 2), (2, 2), (4, 2), (1, 3), (2, 3), (1, 4), (2, 4)])
+@pytest.mark.parametrize("rows,gather,split", [(1, 1, 0), (1, 2, 0), (2, 2, 0), (4, 2, 0), (1, 3, 0), (2, 3, 0),
+                                                (1, 4, 0), (2, 4, 0), (2, 2, 1), (2, 2, 2)])
 @pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n", [12, 17])
-def test_tc_threads_per_group(n, k, rows, gather):
+def test_tc_threads_per_group(n, k, rows, gather, split):
     """The FP16 tensor-core kernel with one, two or four threads per group
     (row), with tiles staged through shared memory (gather 1, 4 and 5
     targets) or gathered per thread one tile ahead (gather 2), not ahead
@@ -137,6 +138,7 @@ def test_tc_threads_per_group(n, k, rows, gather):
     o = qs.qs_default_opts()
     o.tc_row_threads = rows
     o.tc_gather = gather
+    o.tc_split_k = split
     init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
     init /= np.linalg.norm(init)
     for qubits in (list(range(n - k, n)), list(range(k)), [0] + list(range(n - k + 1, n))):
