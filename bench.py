@@ -162,7 +162,7 @@ def kernel_name(rec):
         return "k_tile"
     if rec.kind == 4:
         return "k_phase"
-    return f"k_dense_k{rec.k}" + ("_tc" if rec.tc else "")
+    return f"k_dense_k{rec.k}" + ("_tcx" if rec.tc == 2 else ("_tc" if rec.tc else ""))
 
 
 def CALIBRATION_FLAGS(qs):
@@ -405,6 +405,93 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def cpu_model():
+    """The host CPU's model name, as the kernel reports it."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            text = f.read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model", "CPU part"):
+        for line in text.splitlines():
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    return "unknown"
+
+
+def time_oracle_sampled(text, nthreads, target_s):
+    """Wall time of the FP64 oracle on one circuit with `nthreads` threads:
+    the first g gates are timed (g >= 3, grown until the gates take about half
+    of `target_s` or the list ends), the time of an empty circuit of the same
+    width (allocation and |0...0> initialisation) is subtracted, and the
+    per-gate time is extrapolated to the whole gate list.
+    Returns (seconds, gates timed, gates in total, extrapolated)."""
+    import oracle
+    lines = text.strip().split("\n")
+    head, body = lines[:2], lines[2:]
+    empty = "\n".join(head) + "\n"
+    g, per_gate, timed = min(3, len(body)), 0.0, 0
+    while True:
+        t0 = time.perf_counter()
+        oracle.simulate(empty, nthreads=nthreads)
+        t_init = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.simulate("\n".join(head + body[:g]) + "\n", nthreads=nthreads)
+        t = time.perf_counter() - t0
+        per_gate, timed = max(t - t_init, 1e-9) / g, g
+        if t - t_init >= 0.5 * target_s or g >= len(body):
+            break
+        g = min(len(body), max(g + 1, int(target_s / max(per_gate, 1e-6))))
+    if timed == len(body):
+        return per_gate * timed, timed, len(body), False
+    return per_gate * len(body), timed, len(body), True
+
+
+def run_oracle_bench(args):
+    """Wall time of the FP64 oracle on the host cores, one thread and all
+    threads: the n=12 layered circuits (whole), the n=28 benchmark circuits,
+    the n=26 U3 layers and the n=30 benchmark circuits (first gates timed,
+    extrapolated by gate count). Own JSON line; no GPU is used."""
+    import oracle
+    oracle.build()
+    nmax = oracle.max_threads()
+    items = []
+    for i in range(10):
+        n, gates = cg.layered_swaps_circuit(i)
+        items.append((f"layered n=12 seed {i}", cg.to_qasm(n, gates), True))
+    for m in (28, 30):
+        for name, text in workload(m):
+            items.append((f"{name} n={m}", text, False))
+    _, u3 = cg.u3_entangler_circuit(n=26, layers=40)
+    items.append(("u3 layers n=26", cg.to_qasm(26, u3), False))
+    rows = []
+    for label, text, whole in items:
+        row = {"circuit": label}
+        for nt in (1, nmax):
+            if whole:
+                secs = float("inf")
+                for _ in range(3):  # best of 3: the first call also starts the thread pool
+                    t0 = time.perf_counter()
+                    oracle.simulate(text, nthreads=nt)
+                    secs = min(secs, time.perf_counter() - t0)
+                g = len(text.strip().split("\n")) - 2
+                timed, total, extrap = g, g, False
+            else:
+                secs, timed, total, extrap = time_oracle_sampled(text, nt, args.oracle_target_s)
+            row[f"s_{nt}t"] = round(secs, 4)
+            row[f"gates_timed_{nt}t"] = timed
+            row["gates"] = total
+            row[f"extrapolated_{nt}t"] = extrap
+        rows.append(row)
+        print(json.dumps({"progress": row}), file=sys.stderr, flush=True)
+    line = {"config": "oracle", "cpu": cpu_model(), "nproc": os.cpu_count(), "threads_all": nmax,
+            "rows": rows,
+            "note": "FP64 oracle (plain gate-by-gate definition) wall time on the host cores with 1 and all "
+                    "threads; wide circuits: the first gates are timed after subtracting the empty-circuit "
+                    "(allocation + initialisation) time and extrapolated by gate count"}
+    print(json.dumps(line), flush=True)
+
+
 CASES = ("tc6", "tc5", "tc4", "dense3", "diag10", "phase", "tile", "permute", "probs")
 
 
@@ -422,6 +509,7 @@ def run_case(args):
     opts.tc_row_threads = args.tc_rows
     opts.tc_gather = args.tc_gather
     opts.tc_split_k = args.tc_split_k
+    opts.tc_exchange = args.tc_exchange
     if k:
         qubits = [1, 6, 11, 16, 21, 24][:k] if n > 24 else list(range(0, 2 * k, 2))
         if args.targets:
@@ -450,7 +538,16 @@ def run_case(args):
     else:
         gates = []
         flags = qs.QS_PLAIN
-    st = qs.qs_alloc_state(n, qs.QS_C64)
+    buf = None
+    if args.random_state:
+        # amplitudes of a random state (the all-zero rows of a basis state
+        # make DRAM traffic unrepresentatively cheap)
+        g = torch.Generator(device="cuda").manual_seed(1234)
+        buf = torch.randn(1 << n, dtype=torch.complex64, device="cuda", generator=g)
+        buf /= torch.linalg.vector_norm(buf)
+        st = qs.qs_attach_state(buf.data_ptr(), n, qs.QS_C64)
+    else:
+        st = qs.qs_alloc_state(n, qs.QS_C64)
     arr = qs.gates_to_array(gates)
     recs = []
     for _ in range(args.launches):
@@ -724,13 +821,17 @@ def main():
     ap.add_argument("--tc-rows", type=int, default=0, help="threads per group of the FP16 tensor-core kernel (--case)")
     ap.add_argument("--tc-gather", type=int, default=0, help="tensor-core tiles: 1 staged, 2 per-thread gathers (--case)")
     ap.add_argument("--tc-split-k", type=int, default=0, help="6-target tensor-core blocks: 1 split K, 2 whole K (--case)")
+    ap.add_argument("--random-state", action="store_true", help="--case: start from a random state, not |0...0>")
+    ap.add_argument("--tc-exchange", type=int, default=0,
+                    help="4/5-target tensor-core blocks: 0 lane exchange where it pays, 1 never, 2 always (--case)")
     ap.add_argument("--targets", default="", help="comma-separated target qubits for --case")
     ap.add_argument("--tc-precision", type=int, default=0, help="tensor-core operands: 0 two FP16 halves, 1 3xTF32")
-    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32", "ablation"],
+    ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32", "ablation", "oracle"],
                     help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
     ap.add_argument("--train-circuits", type=int, default=60)
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--qft-max", type=int, default=32, help="ablation: widest QFT of the virtual-swap table")
+    ap.add_argument("--oracle-target-s", type=float, default=3.0, help="oracle: seconds of gates timed per sample")
     args = ap.parse_args()
     if args.case:
         run_case(args)
@@ -746,6 +847,9 @@ def main():
         return
     if args.config == "ablation":
         run_ablation_bench(args)
+        return
+    if args.config == "oracle":
+        run_oracle_bench(args)
         return
     if args.warmup < 3:
         args.warmup = 3

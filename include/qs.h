@@ -130,7 +130,11 @@ typedef struct {
                            the thread-per-group kernel instead of warp-wide loads and shuffles (c64) */
   int tc_split_k;       /* 6-target tensor-core blocks: 1 = K in two halves through 96 KB of shared
                            memory (two CTAs per SM), 2 = whole K (128 KB, one CTA); 0 = default */
-  int reserved[1];
+  int tc_exchange;      /* 4- and 5-target tensor-core blocks (FP16 halves, one thread per group):
+                           0 = lane-exchange gathers where a warp's plain gather would read runs
+                           shorter than 64 bytes (a target among bits 1, 2 with the bits below it
+                           not all free); 1 = never; 2 = wherever the layout allows (bit 0 not a
+                           control, at most two lane/register exchanges) */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);
@@ -207,7 +211,7 @@ typedef struct {
   uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) /
                         tile qubits (tile pass) */
   uint8_t nctrl;     /* control bits that must be 1: only 2^(n-nctrl) amplitudes move */
-  uint8_t tc;        /* 1 if it ran on the tensor cores */
+  uint8_t tc;        /* 1 if it ran on the tensor cores, 2 if so with lane-exchange gathers */
   int8_t qubits[QS_MAX_DIAG]; /* physical qubits ascending, -1 padded; for a tile pass the
                                  tile's qubits above its contiguous low bits */
   uint8_t meta;      /* 0 one-qubit gate, 1 two-qubit gate, 3 swap, 4 fused block,

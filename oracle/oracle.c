@@ -263,7 +263,8 @@ int oracle_count(const char *text, int *n_out, int *gates_out) {
  * init: optional initial state (same layout); NULL means |0...0>.
  * perm_out: n ints, logical qubit -> physical bit after absorbing every SWAP
  * as a relabelling (composition of the SWAP transpositions).
- * nthreads <= 0 keeps the OpenMP default. Returns 0 or a negative error. */
+ * nthreads <= 0 keeps the OpenMP default; a positive count holds for this call
+ * only. Returns 0 or a negative error. */
 int oracle_simulate(const char *text, int n_expected, const double *init, double *out,
                     int *perm_out, int nthreads) {
   int n = 0, count = 0;
@@ -275,6 +276,7 @@ int oracle_simulate(const char *text, int n_expected, const double *init, double
   rc = parse(text, &n, gates, count, &count);
   if (rc) { free(gates); return rc; }
 #ifdef _OPENMP
+  const int prev_threads = omp_get_max_threads();
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
   (void)nthreads;
@@ -298,6 +300,9 @@ int oracle_simulate(const char *text, int n_expected, const double *init, double
   }
   if (perm_out) for (int q = 0; q < n; q++) perm_out[q] = perm[q];
   free(gates);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(prev_threads);  /* the count applies to this call only */
+#endif
   return 0;
 }
 

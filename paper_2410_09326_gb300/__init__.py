@@ -66,7 +66,7 @@ class qs_opts(ctypes.Structure):
                 ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
                 ("tile_k", ctypes.c_int), ("tc_row_threads", ctypes.c_int),
                 ("tc_gather", ctypes.c_int), ("fuse_lookahead", ctypes.c_int),
-                ("no_shuffles", ctypes.c_int), ("tc_split_k", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("no_shuffles", ctypes.c_int), ("tc_split_k", ctypes.c_int), ("tc_exchange", ctypes.c_int)]
 
 
 class qs_class_table(ctypes.Structure):

@@ -610,7 +610,7 @@ void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_recor
   r.kind = (uint8_t)b.kind;
   r.k = (uint8_t)b.k;
   r.nctrl = (uint8_t)b.nctrl;
-  r.tc = b.tc ? 1 : 0;
+  r.tc = b.tc ? (b.tc_xg ? 2 : 1) : 0;
   for (int j = 0; j < QS_MAX_DIAG; j++) r.qubits[j] = j < b.k ? (int8_t)b.q[j] : (int8_t)-1;
   if (b.kind == BK_TILE)
     for (int j = 0; j < QS_MAX_DIAG; j++)
@@ -676,6 +676,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
   if (opts.tc_split_k < 0 || opts.tc_split_k > 2) {
     err = "opts.tc_split_k out of range (0..2)";
+    return QS_EINVAL;
+  }
+  if (opts.tc_exchange < 0 || opts.tc_exchange > 2) {
+    err = "opts.tc_exchange out of range (0..2)";
     return QS_EINVAL;
   }
   if (opts.tc_gather < 0 || opts.tc_gather > 4) {
@@ -855,6 +859,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     b.tc_splitk = b.tc && b.k == 6 && b.tc_rows == 2 && opts.tc_split_k == 1;
     b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
     b.tc_prefetch = opts.tc_gather == 3 ? 0 : (opts.tc_gather == 4 ? 2 : 1);
+    // lane-exchange gathers where the plain gather reads short runs
+    TcXLayout xl;
+    b.tc_xg = b.tc && !tf32 && !b.tc_staged && b.tc_rows == 1 && b.tc_prefetch == 1 && opts.tc_exchange != 1 &&
+              (opts.tc_exchange == 2 || tc_exchange_pays(b)) && tc_exchange_layout(n, b, xl);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;

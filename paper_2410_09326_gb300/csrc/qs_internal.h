@@ -64,6 +64,7 @@ struct Block {
   int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
   bool tc_splitk = false;         // 6-target tensor-core blocks: K in two halves (two CTAs per SM)
+  bool tc_xg = false;             // 4/5-target tensor-core blocks: lane-exchange gathers (tc16.cu)
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,
@@ -77,6 +78,32 @@ struct Block {
   std::vector<double> ph_a, ph_b;
   double ph_c = 0;
 };
+
+// Lane-exchange layout of a 4- or 5-target FP16 tensor-core block (tc16.cu).
+// A warp owns the sub-cube of 32 groups spanned by the targets and the five
+// lowest free bits. It loads it in address order -- element bit of each
+// 16-byte load = bit 0, lane bits = the next five bits of the sub-cube,
+// register bits = the rest -- and then exchanges bits between positions with
+// warp shuffles until the lane bits hold the free bits and the element and
+// register bits hold the targets, i.e. every lane holds one whole group in
+// "slot" order (slot bit 0 = element, slot bit 1 + j = register bit j).
+struct TcXLayout {
+  int lbit[5];       // physical bit of lane bit i, as loaded
+  int rbit[5];       // physical bit of register bit j, as loaded (k - 1 used)
+  int la;            // lane bit exchanged with the element bit, -1 if bit 0 is a target
+  int nswb;          // lane bits lb[i] exchanged with register bits i (i < nswb <= 2)
+  int lb[2];
+  int slot_mat[6];   // slot bit -> position of its target in the block's ascending list
+  int nf;            // targets, controls and the five lowest free bits, ascending
+  int fixed[kMaxFixed];
+};
+// False when the block cannot take the layout: not 4 or 5 targets, bit 0 a
+// control, fewer than 7 free bits among n (whole tiles of 128 groups), more
+// than two lane/register exchanges, or too many fixed bits.
+bool tc_exchange_layout(int n, const Block &b, TcXLayout &x);
+// True where a warp's plain thread-per-group gather reads runs shorter than
+// 64 bytes per load instruction.
+bool tc_exchange_pays(const Block &b);
 
 // Index of the pair (j, l), j < l < w, in a row-order upper triangle.
 inline size_t tri_index(int j, int l, int w) { return (size_t)j * (2 * w - j - 1) / 2 + (l - j - 1); }

@@ -20,6 +20,8 @@
 // 2 x 4^(K+1) x 2 B: 20 KB (K=4), 48 KB (K=5), 128 KB (K=6).
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
+#include <vector>
 
 #include <cuda_fp16.h>
 
@@ -337,6 +339,254 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
   if (aborted) {
     // MMAs may still be in flight: make sure their completion is signalled,
     // give them a bounded chance to land, then return the columns
+    if (tid == 0) mma_commit(mbar_a);
+    mbar_wait(mbar_a, phase ^ 1);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// Lane-exchange variant (K = 4, 5; one thread per group; the next tile in
+// flight during the MMAs). Where targets sit among the lowest bits, the
+// thread-per-group gather above reads short runs per load instruction (16 or
+// 32 bytes when bit 1 or 2 is a target), so a warp touches many sectors per
+// instruction. Here warp w of a tile owns the sub-cube of its 32 groups
+// (targets + the five lowest free bits; the other bits fixed per warp item)
+// and loads it in address order: 16-byte loads whose element bit is bit 0,
+// lanes over the next five bits, registers over the rest. Warp shuffles then
+// exchange position bits -- the element bit with a lane bit (half of every
+// register moves), lane bits with register bits (half of the registers
+// move) -- until each lane holds one whole group, its amplitudes in slot
+// order (slot bit 0 = element bit, 1 + j = register bit j). B is built on the
+// host with its rows and columns in the same slot order, so the product comes
+// out in slot order, the same exchanges (involutions on disjoint bit pairs)
+// restore the load layout 8 slots at a time, and the warp stores as it loaded.
+struct TcXParam {
+  long long n_tiles;          // tiles of 128 groups = 4 warp items of 32
+  unsigned long long cmask;
+  int nf;                     // fixed bits of the warp item index
+  int fixed[kMaxFixed];
+  int lbit[5];                // physical bit of lane bit i (load layout)
+  int rbit[5];                // physical bit of register bit j (load layout)
+  int la;                     // lane bit exchanged with the element bit, -1: none
+  int nswb;                   // lane bits lb[i] exchanged with register bits i
+  int lb[2];
+  int withhold_commit;
+};
+
+template <int K>
+__global__ void __launch_bounds__(kTcThreads, Tc16Occ<K, 1, 1>::value)
+    k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
+                  int *__restrict__ err) {
+  constexpr int D = 1 << K;
+  constexpr int NV = D / 2;    // 16-byte registers per lane
+  constexpr int RB = K - 1;    // register bits
+  constexpr int KR = 2 * D;
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t NCOLS = 2 * KR;
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA_hi = smem;
+  unsigned char *sA_lo = smem + A_BYTES;
+  unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t mbar_a = smem_addr(&mbar);
+  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+  const uint32_t row_off = (uint32_t)(tid >> 3) * SBO + (uint32_t)(tid & 7) * 16u;
+
+  uint64_t lane_off = 0;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
+  uint64_t roff[RB];
+#pragma unroll
+  for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
+  auto offset = [&](int rr) {
+    uint64_t o = lane_off;
+#pragma unroll
+    for (int j = 0; j < RB; j++)
+      if ((rr >> j) & 1) o += roff[j];
+    return o;
+  };
+  const int la = p.la, nswb = p.nswb;
+  const bool up_a = la >= 0 && ((lane >> (la & 31)) & 1);
+  const unsigned ma = 1u << (la & 31);
+  // the exchanges, on N consecutive registers starting at a multiple of 4
+  // (register bits 0 and 1 of the pairs lie inside any such run)
+  auto exchange = [&](float4 *w, auto n_regs) {
+    constexpr int N = decltype(n_regs)::value;
+    if (la >= 0) {
+#pragma unroll
+      for (int r = 0; r < N; r++) {
+        // lane bit 0 keeps the element-0 half and trades its element-1 half
+        // for the partner's element-0 half; lane bit 1 the other way round
+        const float s0 = up_a ? w[r].x : w[r].z, s1 = up_a ? w[r].y : w[r].w;
+        const float r0 = __shfl_xor_sync(0xffffffffu, s0, ma), r1 = __shfl_xor_sync(0xffffffffu, s1, ma);
+        if (up_a) {
+          w[r].x = r0;
+          w[r].y = r1;
+        } else {
+          w[r].z = r0;
+          w[r].w = r1;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      if (i >= nswb) break;
+      const int lbi = p.lb[i];
+      const bool up = (lane >> lbi) & 1;
+#pragma unroll
+      for (int r = 0; r < N; r++) {
+        if ((r >> i) & 1) continue;
+        const int r2 = r | (1 << i);
+        const float4 snd = up ? w[r] : w[r2];
+        float4 rcv;
+        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
+        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
+        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
+        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
+        if (up) w[r] = rcv;
+        else w[r2] = rcv;
+      }
+    }
+  };
+
+  uint32_t phase = 0;
+  bool aborted = false;
+  long long tile = blockIdx.x;
+  float4 v[NV];
+  uint64_t base = 0;
+  bool valid = false;
+  auto gather = [&](long long t) {
+    valid = t < p.n_tiles;  // uniform over the CTA
+    base = valid ? (insert_zeros((uint64_t)(t * 4 + warp), p.fixed, p.nf) | p.cmask) : 0;
+#pragma unroll
+    for (int r = 0; r < NV; r++)
+      v[r] = valid ? *reinterpret_cast<const float4 *>(a + base + offset(r)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  gather(tile);
+
+  for (; tile < p.n_tiles; tile += gridDim.x) {
+    exchange(v, std::integral_constant<int, NV>{});
+    float mx = 0.f, nin = 0.f;
+#pragma unroll
+    for (int r = 0; r < NV; r++) {
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[r].x), fabsf(v[r].y)), fmaxf(fabsf(v[r].z), fabsf(v[r].w))));
+      nin = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, fmaf(v[r].z, v[r].z, fmaf(v[r].w, v[r].w, nin))));
+    }
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+    // slots 4c..4c+3 (registers 2c, 2c + 1) fill the 16-byte row of core matrix c
+#pragma unroll
+    for (int c = 0; c < D / 4; c++) {
+      const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
+                          v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
+      uint4 hi, lo;
+      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+        const float2 hf = __half22float2(hh);
+        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
+        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
+      }
+      *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
+      *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ks++) {
+        const uint32_t koff = (uint32_t)ks * 2u * LBO;
+        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        mma_f16(tmem, dah, dbh, IDESC, acc);
+        mma_f16(tmem + KR, dah, dbl, IDESC, acc);
+        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+      }
+      if (!p.withhold_commit) mma_commit(mbar_a);
+    }
+    const uint64_t cur_base = base;
+    const bool cur_valid = valid;
+    gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    const bool ok = mbar_wait(mbar_a, phase);
+    phase ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      aborted = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    float nout = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < KR / 16; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+    // 8 slots (4 registers) at a time: scale, exchange back, store
+#pragma unroll
+    for (int hh = 0; hh < KR / 16; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float4 y[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
+                           (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
+                           (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
+                           (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
+      exchange(y, std::integral_constant<int, 4>{});
+      if (cur_valid) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) {
     if (tid == 0) mma_commit(mbar_a);
     mbar_wait(mbar_a, phase ^ 1);
   }
@@ -722,6 +972,41 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   return cudaGetLastError();
 }
 
+template <int K>
+cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                      cudaStream_t s) {
+  TcXParam p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_tiles = (1ll << (n - K - b.nctrl)) / kTcThreads;
+  p.cmask = b.cmask;
+  p.nf = x.nf;
+  for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
+  for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
+  for (int j = 0; j < K - 1; j++) p.rbit[j] = x.rbit[j];
+  p.la = x.la;
+  p.nswb = x.nswb;
+  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
+  const size_t smem = tc16_smem_bytes<K>();
+  static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc16x<K>, kTcThreads, smem);
+    const int tmem_cap = 512 / (4 << K);
+    per_sm = occ > Tc16Occ<K, 1, 1>::value ? Tc16Occ<K, 1, 1>::value : occ;
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms * per_sm;
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16x<K><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t tc16_b_bytes(int k) { return 2u * (size_t)(2 << k) * (size_t)(2 << k) * 2u; }
@@ -732,12 +1017,32 @@ void tc16_build_b(const Block &b, void *out) {
   const int D = 1 << b.k, KR = 2 * D;
   const size_t n = (size_t)KR * KR;
   __half *h = (__half *)out;
+  // lane-exchange blocks take the matrix with rows and columns in slot
+  // order: entry (rho, sigma) = U(pi(rho), pi(sigma)), pi(rho) = sum over the
+  // slot bits set of 1 << (their target's position). The layout depends on the
+  // targets and controls only (the planner checked that n admits it), so any
+  // n above the fixed bits gives the same slots.
+  std::vector<cd> slot_mat;
+  const std::vector<cd> *m = &b.mat;
+  TcXLayout x;
+  if (b.tc_xg && tc_exchange_layout(64, b, x)) {
+    auto pi = [&](int rho) {
+      int s = 0;
+      for (int j = 0; j < b.k; j++)
+        if ((rho >> j) & 1) s |= 1 << x.slot_mat[j];
+      return s;
+    };
+    slot_mat.resize((size_t)D * D);
+    for (int r = 0; r < D; r++)
+      for (int c = 0; c < D; c++) slot_mat[(size_t)r * D + c] = b.mat[(size_t)pi(r) * D + pi(c)];
+    m = &slot_mat;
+  }
   auto at = [&](int row, int col) {
     return (size_t)(row >> 3) * (KR / 8) * 64 + (size_t)(col >> 3) * 64 + (row & 7) * 8 + (col & 7);
   };
   for (int r = 0; r < D; r++)
     for (int s = 0; s < D; s++) {
-      const cd u = b.mat[(size_t)r * D + s];
+      const cd u = (*m)[(size_t)r * D + s];
       const float vals[2][2] = {{(float)u.real(), (float)-u.imag()}, {(float)u.imag(), (float)u.real()}};
       for (int i = 0; i < 2; i++)
         for (int j = 0; j < 2; j++) {
@@ -751,6 +1056,12 @@ void tc16_build_b(const Block &b, void *out) {
 }
 
 cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+  if (b.tc_xg) {
+    // B was built in slot order: no other kernel can take this block
+    TcXLayout x;
+    if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
+    return b.k == 4 ? run_tc16x<4>(a, n, b, x, dev_b, err, s) : run_tc16x<5>(a, n, b, x, dev_b, err, s);
+  }
   if (b.tc_staged && (b.k == 4 || b.k == 5)) {
     static thread_local TcStageParam sp;  // large: kept off the stack; the launch copies it
     if (stage_param(n, b, sp)) return b.k == 4 ? run_tc16s<4>(a, sp, dev_b, err, s) : run_tc16s<5>(a, sp, dev_b, err, s);
@@ -780,4 +1091,87 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
 }
 
 }  // namespace kern
+
+bool tc_exchange_pays(const Block &b) {
+  if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5)) return false;
+  uint64_t tmask = 0;
+  for (int j = 0; j < b.k; j++) tmask |= 1ull << b.q[j];
+  // the plain gather: lanes over the five lowest free bits, 16-byte pairs
+  // when bit 0 is a target; a run is the span of consecutive low bits covered
+  uint64_t covered = tmask & 1ull;
+  for (int q = 0, nfree = 0; q < 64 && nfree < 5; q++)
+    if (!(((tmask | b.cmask) >> q) & 1)) {
+      covered |= 1ull << q;
+      nfree++;
+    }
+  int run = 0;
+  while (run < 64 && ((covered >> run) & 1)) run++;
+  return (8 << run) < 64;
+}
+
+bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
+  if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5) || (b.cmask & 1ull)) return false;
+  const int K = b.k;
+  if (n - K - b.nctrl < 7) return false;  // whole tiles of 128 groups
+  uint64_t tmask = 0;
+  for (int j = 0; j < K; j++) tmask |= 1ull << b.q[j];
+  const uint64_t used = tmask | b.cmask;
+  uint64_t cube = tmask;  // the warp's sub-cube: targets + the five lowest free bits
+  for (int q = 0, nfree = 0; q < 64 && nfree < 5; q++)
+    if (!((used >> q) & 1)) {
+      cube |= 1ull << q;
+      nfree++;
+    }
+  int bits[16], nb = 0;
+  for (int q = 0; q < 64; q++)
+    if ((cube >> q) & 1) bits[nb++] = q;
+  if (nb != K + 5 || bits[0] != 0) return false;
+  auto is_t = [&](int q) { return ((tmask >> q) & 1) != 0; };
+  int lpost[5];
+  for (int i = 0; i < 5; i++) x.lbit[i] = lpost[i] = bits[1 + i];
+  // element bit free: exchange it with the lowest lane bit holding a target
+  // (one exists: K targets, K - 1 register bits)
+  x.la = -1;
+  int epost = 0;
+  if (!is_t(0)) {
+    for (int i = 0; i < 5 && x.la < 0; i++)
+      if (is_t(x.lbit[i])) x.la = i;
+    if (x.la < 0) return false;
+    epost = x.lbit[x.la];
+    lpost[x.la] = 0;
+  }
+  // lane bits still holding targets <-> register bits holding free bits
+  // (equally many); the latter become register bits 0, 1
+  int tl[5], ntl = 0, fr[4], nfr = 0, tr[4], ntr = 0;
+  for (int i = 0; i < 5; i++)
+    if (is_t(lpost[i])) tl[ntl++] = i;
+  for (int j = 0; j < K - 1; j++) {
+    const int q = bits[6 + j];
+    if (is_t(q)) tr[ntr++] = q;
+    else fr[nfr++] = q;
+  }
+  if (ntl != nfr || ntl > 2) return false;
+  x.nswb = ntl;
+  int rb = 0;
+  for (int i = 0; i < nfr; i++) x.rbit[rb++] = fr[i];
+  for (int i = 0; i < ntr; i++) x.rbit[rb++] = tr[i];
+  for (int i = 0; i < ntl; i++) x.lb[i] = tl[i];
+  // the target each slot bit holds once the exchanges are done
+  int slot_phys[6];
+  slot_phys[0] = epost;
+  for (int j = 0; j < K - 1; j++) slot_phys[1 + j] = j < ntl ? lpost[tl[j]] : x.rbit[j];
+  for (int s = 0; s < K; s++) {
+    x.slot_mat[s] = -1;
+    for (int t = 0; t < K; t++)
+      if (b.q[t] == slot_phys[s]) x.slot_mat[s] = t;
+    if (x.slot_mat[s] < 0) return false;
+  }
+  const uint64_t fixedm = cube | b.cmask;
+  if (__builtin_popcountll(fixedm) > kMaxFixed) return false;
+  x.nf = 0;
+  for (int q = 0; q < 64; q++)
+    if ((fixedm >> q) & 1) x.fixed[x.nf++] = q;
+  return true;
+}
+
 }  // namespace qs

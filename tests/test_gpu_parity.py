@@ -17,6 +17,7 @@ import pytest
 import circuitgen as cg
 import oracle
 import paper_2410_09326_gb300 as qs
+from lane_exchange_rule import lane_exchange_expected
 
 pytestmark = pytest.mark.gpu
 
@@ -161,6 +162,61 @@ def test_tc_threads_per_group(n, k, rows, gather, split):
         assert np.linalg.norm(got - want) <= 1e-5
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("ctrl", [None, 5, 0])
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n", [12, 17])
+def test_tc_lane_exchange(n, k, ctrl, mode):
+    """4- and 5-target tensor-core blocks with lane-exchange gathers
+    (opts.tc_exchange: 0 automatic, 1 never, 2 wherever the layout allows)
+    on low-bit target patterns (no exchange, the element bit's exchange, one
+    or two lane/register exchanges, three: plain kernel), without a control,
+    with a control on bit 5 and with bit 0 a control (no exchange layout),
+    one tile (n = 12) and many (n = 17), from a random state; the record's tc
+    field says which kernel ran (2 = lane exchange)."""
+    rng = cg.SplitMix64(1300 + 10 * k + n + (ctrl or 0))
+    o = qs.qs_default_opts()
+    o.tc_exchange = mode
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    patterns = ([7, 8, 9, 10, 11], [1, 7, 8, 9, 10], [2, 7, 8, 9, 10], [3, 7, 8, 9, 10], [0, 7, 8, 9, 10],
+                [0, 1, 8, 9, 10], [1, 2, 8, 9, 10], [2, 3, 8, 9, 10], [1, 2, 3, 9, 10], [0, 1, 2, 3, 9])
+    kinds = set()
+    for pattern in patterns:
+        qubits = pattern[:k]
+        if ctrl is not None and ctrl in qubits:
+            continue
+        ctrls = [] if ctrl is None else [ctrl]
+        if ctrl is None:
+            gates = []
+            for _ in range(2):
+                gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        else:
+            gates = []  # the random state already spreads over the control's values
+            for _ in range(2):
+                gates += [("cu3", [ctrl, q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("ccx", [ctrl, a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(k + len(ctrls)) | qs.QS_TC, o)
+            _, recs = qs.qs_profile(st)
+            blk = [r for r in recs if r.kind == 0 and r.k == k]
+            assert len(blk) == 1 and [int(x) for x in blk[0].qubits[:k]] == qubits and blk[0].nctrl == len(ctrls)
+            fits, pays = lane_exchange_expected(n, qubits, ctrls)
+            expect = fits and (mode == 2 or (mode == 0 and pays))
+            assert blk[0].tc == (2 if expect else 1), (qubits, ctrl, mode, blk[0].tc)
+            kinds.add(int(blk[0].tc))
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl, mode)
+    if mode == 2 and ctrl != 0 and n == 17:
+        assert 2 in kinds
+
+
 @pytest.mark.parametrize("shuffles", [0, 1])
 @pytest.mark.parametrize("n", [9, 12, 16])
 def test_low_target_warp_shuffle_kernel(n, shuffles):
@@ -272,7 +328,7 @@ def test_tc_blocks_really_run_on_tensor_cores():
     try:
         qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS["vswap_k5_tc_diag"] | qs.QS_PROFILE)
         summ, recs = qs.qs_profile(st)
-        assert any(r.tc for r in recs) and all(r.tc == (r.kind == 0 and r.k in (4, 5)) for r in recs)
+        assert any(r.tc for r in recs) and all(bool(r.tc) == (r.kind == 0 and r.k in (4, 5)) for r in recs)
     finally:
         qs.qs_free_state(st)
 

@@ -19,6 +19,7 @@ import circuitgen as cg
 import oracle
 import paper_2410_09326_gb300 as qs
 from paper_2410_09326_gb300 import build as qbuild
+from lane_exchange_rule import lane_exchange_expected
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -257,6 +258,43 @@ def test_rules_select_follows_the_paper_rules():
     _, operm = oracle.simulate(cg.to_qasm(n, gates))
     assert list(perm) == list(operm)  # SWAPs were absorbed
     assert len(recs) < len(gates) // 2  # and gates were merged
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_lane_exchange_choice_on_benchmark_circuits(mode):
+    """The planner marks a 4/5-target tensor-core block for lane-exchange
+    gathers (record tc = 2) exactly where the rule says: automatic mode where
+    the plain gather reads short runs, never with mode 1, wherever the layout
+    fits with mode 2. Checked on every block of the n = 30 benchmark circuits
+    and of 40 random circuits at n = 12..20."""
+    o = qs.qs_default_opts()
+    o.tc_exchange = mode
+    cases = []
+    c = cg.benchmark_circuits(n=30)
+    cases += [(30, c["ghz"][1]), (30, c["qft"][1]), (30, c["random"][1])]
+    for i in range(40):
+        rng = cg.SplitMix64(7000 + i)
+        n = 12 + i % 9
+        gates = cg.random_layered(n, 4, rng, one_q=("u3",), two_q=("cx", "cz"))
+        for _ in range(3 * n):  # controlled gates: blocks with controls
+            q = rng.shuffle(list(range(n)))[:3]
+            gates.append(("ccx", q) if rng.randint(2) else ("cu3", q[:2], [rng.uniform(0, 6.28) for _ in range(3)]))
+        cases.append((n, gates))
+    seen = {1: 0, 2: 0}
+    for n, gates in cases:
+        for k in (4, 5):
+            recs, _, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC,
+                                    opts=o)
+            for r in recs:
+                if r.kind != 0 or r.k not in (4, 5):
+                    continue
+                qubits = [int(x) for x in r.qubits[:r.k]]
+                ctrls = [q for q in range(n) if (r.cmask >> q) & 1]
+                fits, pays = lane_exchange_expected(n, qubits, ctrls)
+                expect = fits and (mode == 2 or (mode == 0 and pays))
+                assert r.tc == (2 if expect else 1), (n, qubits, ctrls, mode)
+                seen[r.tc] += 1
+    assert seen[1] > 0 and (mode == 1 or seen[2] > 0)
 
 
 def test_measured_select_with_priors_prefers_wide_tensor_core_blocks():
