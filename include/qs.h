@@ -131,10 +131,10 @@ typedef struct {
   int tc_split_k;       /* 6-target tensor-core blocks: 1 = K in two halves through 96 KB of shared
                            memory (two CTAs per SM), 2 = whole K (128 KB, one CTA); 0 = default */
   int tc_exchange;      /* 4- and 5-target tensor-core blocks (FP16 halves, one thread per group):
-                           0 = lane-exchange gathers where a warp's plain gather would read runs
-                           shorter than 64 bytes (a target among bits 1, 2 with the bits below it
-                           not all free); 1 = never; 2 = wherever the layout allows (bit 0 not a
-                           control, at most two lane/register exchanges) */
+                           0 = lane-exchange gathers where they measured faster (every 5-target
+                           block, 4-target blocks with two or more targets among bits 1..3);
+                           1 = never; 2 = wherever the layout allows (bit 0 not a control, at
+                           most two lane/register exchanges, whole tiles of 128 groups) */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

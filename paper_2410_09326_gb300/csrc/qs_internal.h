@@ -101,8 +101,9 @@ struct TcXLayout {
 // control, fewer than 7 free bits among n (whole tiles of 128 groups), more
 // than two lane/register exchanges, or too many fixed bits.
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x);
-// True where a warp's plain thread-per-group gather reads runs shorter than
-// 64 bytes per load instruction.
+// True where the exchange kernel measured faster than the plain
+// thread-per-group gather: every 5-target block, 4-target blocks with two
+// or more targets among bits 1..3.
 bool tc_exchange_pays(const Block &b);
 
 // Index of the pair (j, l), j < l < w, in a row-order upper triangle.

@@ -1094,19 +1094,16 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
 
 bool tc_exchange_pays(const Block &b) {
   if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5)) return false;
-  uint64_t tmask = 0;
-  for (int j = 0; j < b.k; j++) tmask |= 1ull << b.q[j];
-  // the plain gather: lanes over the five lowest free bits, 16-byte pairs
-  // when bit 0 is a target; a run is the span of consecutive low bits covered
-  uint64_t covered = tmask & 1ull;
-  for (int q = 0, nfree = 0; q < 64 && nfree < 5; q++)
-    if (!(((tmask | b.cmask) >> q) & 1)) {
-      covered |= 1ull << q;
-      nfree++;
-    }
-  int run = 0;
-  while (run < 64 && ((covered >> run) & 1)) run++;
-  return (8 << run) < 64;
+  // measured on GB300 from random states at n = 28: with 5 targets the
+  // exchange kernel is ahead for every placement (5.77-6.01 vs 5.56-5.72 TB/s
+  // with at most one low target, 4.87-5.79 vs 3.21-4.96 with two or three);
+  // with 4 targets only where two or more targets lie among bits 1..3
+  // (4.89-5.34 vs 3.41-5.29 TB/s), elsewhere the plain gather is ahead
+  // (5.84-6.29 vs 5.59-5.87)
+  if (b.k == 5) return true;
+  int low = 0;
+  for (int j = 0; j < b.k; j++) low += (b.q[j] >= 1 && b.q[j] <= 3) ? 1 : 0;
+  return low >= 2;
 }
 
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {

@@ -7,9 +7,9 @@ def lane_exchange_expected(n, qubits, ctrls):
     """(layout admits the lane exchange, the automatic rule picks it) for a
     block with these targets and controls: bit 0 must not be a control, the
     groups must fill tiles of 128, and after the element bit's exchange at
-    most two lane bits may still hold targets; the rule picks it where the
-    plain gather (lanes over the five lowest free bits, 16-byte pairs when
-    bit 0 is a target) reads runs shorter than 64 bytes."""
+    most two lane bits may still hold targets; the automatic rule picks it
+    for every 5-target block and for 4-target blocks with two or more
+    targets among bits 1..3."""
     t = set(qubits)
     free = [q for q in range(64) if q not in t and q not in ctrls][:5]
     cube = sorted(t | set(free))
@@ -19,8 +19,5 @@ def lane_exchange_expected(n, qubits, ctrls):
         if 0 not in t:
             lanes[[q in t for q in lanes].index(True)] = 0
         fits = sum(q in t for q in lanes) <= 2
-    covered = ({0} & t) | set(free)
-    run = 0
-    while run in covered:
-        run += 1
-    return fits, (8 << run) < 64
+    pays = len(qubits) == 5 or len(t & {1, 2, 3}) >= 2
+    return fits, pays
