@@ -133,8 +133,8 @@ typedef struct {
   int tc_exchange;      /* 4- and 5-target tensor-core blocks (FP16 halves, one thread per group):
                            0 = lane-exchange gathers where they measured faster (every 5-target
                            block, 4-target blocks with two or more targets among bits 1..3);
-                           1 = never; 2 = wherever the layout allows (bit 0 not a control, at
-                           most two lane/register exchanges, whole tiles of 128 groups) */
+                           1 = never; 2 = wherever the layout allows (bit 0 not a control,
+                           whole tiles of 128 groups) */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);

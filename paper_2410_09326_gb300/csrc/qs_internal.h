@@ -82,8 +82,11 @@ struct Block {
 // Lane-exchange layout of a 4- or 5-target FP16 tensor-core block (tc16.cu).
 // A warp owns the sub-cube of 32 groups spanned by the targets and the five
 // lowest free bits. It loads it in address order -- element bit of each
-// 16-byte load = bit 0, lane bits = the next five bits of the sub-cube,
-// register bits = the rest -- and then exchanges bits between positions with
+// 16-byte load = bit 0, lane bits = the next five bits of the sub-cube
+// (where that would leave more than two targets on lane bits after the
+// element bit's exchange, the highest of them trade places with the lowest
+// free register bits), register bits = the rest -- and then exchanges bits
+// between positions with
 // warp shuffles until the lane bits hold the free bits and the element and
 // register bits hold the targets, i.e. every lane holds one whole group in
 // "slot" order (slot bit 0 = element, slot bit 1 + j = register bit j).
@@ -98,8 +101,8 @@ struct TcXLayout {
   int fixed[kMaxFixed];
 };
 // False when the block cannot take the layout: not 4 or 5 targets, bit 0 a
-// control, fewer than 7 free bits among n (whole tiles of 128 groups), more
-// than two lane/register exchanges, or too many fixed bits.
+// control, fewer than 7 free bits among n (whole tiles of 128 groups), or
+// too many fixed bits.
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x);
 // True where the exchange kernel measured faster than the plain
 // thread-per-group gather: every 5-target block, 4-target blocks with two

@@ -1119,13 +1119,31 @@ bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
       cube |= 1ull << q;
       nfree++;
     }
-  int bits[16], nb = 0;
-  for (int q = 0; q < 64; q++)
-    if ((cube >> q) & 1) bits[nb++] = q;
-  if (nb != K + 5 || bits[0] != 0) return false;
+  if (!(cube & 1ull) || __builtin_popcountll(cube) != K + 5) return false;
   auto is_t = [&](int q) { return ((tmask >> q) & 1) != 0; };
+  // lane bits: the five lowest bits of the sub-cube above bit 0 (longest
+  // runs per load); the rest are register bits
+  uint64_t lanes = 0;
+  for (int q = 1, nl = 0; q < 64 && nl < 5; q++)
+    if ((cube >> q) & 1) {
+      lanes |= 1ull << q;
+      nl++;
+    }
+  // targets left on lane bits once the element bit (if free) has taken the
+  // lowest one; above two, the highest of them trade places with the lowest
+  // free register bits (shorter runs per load, fewer exchanges)
+  auto lane_targets = [&]() { return __builtin_popcountll(lanes & tmask) - (is_t(0) ? 0 : 1); };
+  while (lane_targets() > 2) {
+    const uint64_t lt = lanes & tmask, fr = cube & ~lanes & ~tmask & ~1ull;
+    if (!fr) return false;
+    const int hi_t = 63 - __builtin_clzll(lt), lo_f = __builtin_ctzll(fr);
+    lanes = (lanes & ~(1ull << hi_t)) | (1ull << lo_f);
+  }
+  int nl = 0;
+  for (int q = 0; q < 64; q++)
+    if ((lanes >> q) & 1) x.lbit[nl++] = q;
   int lpost[5];
-  for (int i = 0; i < 5; i++) x.lbit[i] = lpost[i] = bits[1 + i];
+  for (int i = 0; i < 5; i++) lpost[i] = x.lbit[i];
   // element bit free: exchange it with the lowest lane bit holding a target
   // (one exists: K targets, K - 1 register bits)
   x.la = -1;
@@ -1142,12 +1160,17 @@ bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
   int tl[5], ntl = 0, fr[4], nfr = 0, tr[4], ntr = 0;
   for (int i = 0; i < 5; i++)
     if (is_t(lpost[i])) tl[ntl++] = i;
-  for (int j = 0; j < K - 1; j++) {
-    const int q = bits[6 + j];
-    if (is_t(q)) tr[ntr++] = q;
-    else fr[nfr++] = q;
-  }
-  if (ntl != nfr || ntl > 2) return false;
+  for (int q = 1; q < 64; q++)
+    if (((cube & ~lanes) >> q) & 1) {
+      if (is_t(q)) {
+        if (ntr < 4) tr[ntr] = q;
+        ntr++;
+      } else {
+        if (nfr < 4) fr[nfr] = q;
+        nfr++;
+      }
+    }
+  if (ntr + nfr != K - 1 || ntl != nfr || ntl > 2) return false;
   x.nswb = ntl;
   int rb = 0;
   for (int i = 0; i < nfr; i++) x.rbit[rb++] = fr[i];
@@ -1170,5 +1193,4 @@ bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
     if ((fixedm >> q) & 1) x.fixed[x.nf++] = q;
   return true;
 }
-
 }  // namespace qs

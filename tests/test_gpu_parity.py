@@ -170,7 +170,8 @@ def test_tc_lane_exchange(n, k, ctrl, mode):
     """4- and 5-target tensor-core blocks with lane-exchange gathers
     (opts.tc_exchange: 0 automatic, 1 never, 2 wherever the layout allows)
     on low-bit target patterns (no exchange, the element bit's exchange, one
-    or two lane/register exchanges, three: plain kernel), without a control,
+    or two lane/register exchanges, targets moved from lane to register bits
+    to keep two), without a control,
     with a control on bit 5 and with bit 0 a control (no exchange layout),
     one tile (n = 12) and many (n = 17), from a random state; the record's tc
     field says which kernel ran (2 = lane exchange)."""
@@ -180,7 +181,8 @@ def test_tc_lane_exchange(n, k, ctrl, mode):
     init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
     init /= np.linalg.norm(init)
     patterns = ([7, 8, 9, 10, 11], [1, 7, 8, 9, 10], [2, 7, 8, 9, 10], [3, 7, 8, 9, 10], [0, 7, 8, 9, 10],
-                [0, 1, 8, 9, 10], [1, 2, 8, 9, 10], [2, 3, 8, 9, 10], [1, 2, 3, 9, 10], [0, 1, 2, 3, 9])
+                [0, 1, 8, 9, 10], [1, 2, 8, 9, 10], [2, 3, 8, 9, 10], [1, 2, 3, 9, 10], [0, 1, 2, 3, 9],
+                [0, 1, 2, 3, 4], [1, 2, 3, 4, 5])
     kinds = set()
     for pattern in patterns:
         qubits = pattern[:k]
