@@ -373,8 +373,13 @@ struct TcXParam {
   int withhold_commit;
 };
 
+// Resident CTAs per SM of the exchange kernel (registers per thread follow).
+template <int K> struct Tc16xOcc {
+  static constexpr int value = K <= 4 ? 4 : 3;
+};
+
 template <int K>
-__global__ void __launch_bounds__(kTcThreads, Tc16Occ<K, 1, 1>::value)
+__global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
     k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                   int *__restrict__ err) {
   constexpr int D = 1 << K;
@@ -997,7 +1002,7 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
     if (e != cudaSuccess) return e;
     const int occ = resident_ctas((const void *)k_dense_tc16x<K>, kTcThreads, smem);
     const int tmem_cap = 512 / (4 << K);
-    per_sm = occ > Tc16Occ<K, 1, 1>::value ? Tc16Occ<K, 1, 1>::value : occ;
+    per_sm = occ > Tc16xOcc<K>::value ? Tc16xOcc<K>::value : occ;
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     configured = dev;
   }
