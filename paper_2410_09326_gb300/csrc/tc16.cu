@@ -374,8 +374,12 @@ struct TcXParam {
 };
 
 // Resident CTAs per SM of the exchange kernel (registers per thread follow).
+// Measured on GB300 from random states at n = 28: spill-free registers beat
+// more resident CTAs -- 5 targets at 2 CTAs (237 registers) ran 5413-6024
+// GB/s, at 3 (168, spilling) 5386-5913, at 4 (128) 4053-4119; 4 targets at
+// 3 CTAs (153 registers) 5508-5858, at 4 (128, spilling) 5344-5728.
 template <int K> struct Tc16xOcc {
-  static constexpr int value = K <= 4 ? 4 : 3;
+  static constexpr int value = K <= 4 ? 3 : 2;
 };
 
 template <int K>
