@@ -79,7 +79,9 @@ struct Block {
   double ph_c = 0;
 };
 
-// Lane-exchange layout of a 4- or 5-target FP16 tensor-core block (tc16.cu).
+// Lane-exchange layout of a 4-, 5- or 6-target FP16 tensor-core block
+// (tc16.cu; 6 targets: two threads per group, each half laid out as a
+// 5-target block with the highest target fixed).
 // A warp owns the sub-cube of 32 groups spanned by the targets and the five
 // lowest free bits. It loads it in address order -- element bit of each
 // 16-byte load = bit 0, lane bits = the next five bits of the sub-cube
@@ -97,10 +99,11 @@ struct TcXLayout {
   int nswb;          // lane bits lb[i] exchanged with register bits i (i < nswb <= 2)
   int lb[2];
   int slot_mat[6];   // slot bit -> position of its target in the block's ascending list
+  int th;            // 6 targets: the highest target, fixed per thread half (slot bit 5); else -1
   int nf;            // targets, controls and the five lowest free bits, ascending
   int fixed[kMaxFixed];
 };
-// False when the block cannot take the layout: not 4 or 5 targets, bit 0 a
+// False when the block cannot take the layout: not 4..6 targets, bit 0 a
 // control, fewer than 7 free bits among n (whole tiles of 128 groups), or
 // too many fixed bits.
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x);

@@ -370,6 +370,7 @@ struct TcXParam {
   int la;                     // lane bit exchanged with the element bit, -1: none
   int nswb;                   // lane bits lb[i] exchanged with register bits i
   int lb[2];
+  int th;                     // 6 targets: the target bit thread half h fixes (the highest)
   int withhold_commit;
 };
 
@@ -598,6 +599,262 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
   if (aborted) {
     if (tid == 0) mma_commit(mbar_a);
     mbar_wait(mbar_a, phase ^ 1);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// Six targets: the same lane exchange, two threads per group and two tiles in
+// flight. Thread (h, r), h = tid / 128, holds the 32 amplitudes of group r
+// whose highest target equals h: warp w and warp w + 4 load the same 32
+// groups' two halves, each exactly as a 5-target exchange warp (the highest
+// target fixed per half). The A operands (64 KB per tile) and the TMEM
+// accumulators (256 columns per tile) are double-buffered, so the MMAs of
+// tile i run while the CTA stores tile i - 1 and gathers tile i + 1: with the
+// 6-target operands one CTA fills an SM, and without the second buffer the
+// SM idled for the MMAs (about a fifth of a tile). Slot bit 5 = the highest
+// target; the row's scale and norms are combined over the two halves through
+// shared memory.
+__global__ void __launch_bounds__(2 * kTcThreads, 1)
+    k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
+                   int *__restrict__ err) {
+  constexpr int NT = 2 * kTcThreads;
+  constexpr int NV = 16;        // 16-byte registers per thread (32 amplitudes)
+  constexpr int RB = 4;         // register bits
+  constexpr int KR = 128;       // real K = N
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;     // one of hi / lo, one tile
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t NCOLS = 512;                  // two tiles x (large + small)
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after both buffers
+  unsigned char *sB = smem + 4 * A_BYTES;
+  __shared__ __align__(8) uint64_t mbar[3];  // per buffer; [2] for the final drain
+  __shared__ uint32_t tmem_slot;
+  __shared__ float red_in[2 * NT];
+  __shared__ float red_out[NT];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int r = tid & 127;
+  const int h = tid >> 7;
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += NT) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int u = 0; u < 3; u++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[u])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  uint64_t lane_off = h ? (1ull << p.th) : 0ull;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
+  uint64_t roff[RB];
+#pragma unroll
+  for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
+  auto offset = [&](int rr) {
+    uint64_t o = lane_off;
+#pragma unroll
+    for (int j = 0; j < RB; j++)
+      if ((rr >> j) & 1) o += roff[j];
+    return o;
+  };
+  const int la = p.la, nswb = p.nswb;
+  const bool up_a = la >= 0 && ((lane >> (la & 31)) & 1);
+  const unsigned ma = 1u << (la & 31);
+  auto exchange = [&](float4 *w, auto n_regs) {
+    constexpr int N = decltype(n_regs)::value;
+    if (la >= 0) {
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        const float s0 = up_a ? w[q].x : w[q].z, s1 = up_a ? w[q].y : w[q].w;
+        const float r0 = __shfl_xor_sync(0xffffffffu, s0, ma), r1 = __shfl_xor_sync(0xffffffffu, s1, ma);
+        if (up_a) {
+          w[q].x = r0;
+          w[q].y = r1;
+        } else {
+          w[q].z = r0;
+          w[q].w = r1;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      if (i >= nswb) break;
+      const int lbi = p.lb[i];
+      const bool up = (lane >> lbi) & 1;
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        if ((q >> i) & 1) continue;
+        const int q2 = q | (1 << i);
+        const float4 snd = up ? w[q] : w[q2];
+        float4 rcv;
+        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
+        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
+        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
+        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
+        if (up) w[q] = rcv;
+        else w[q2] = rcv;
+      }
+    }
+  };
+
+  float4 v[NV];
+  uint64_t base = 0;
+  auto gather = [&](long long t) {
+    const bool ok = t < p.n_tiles;  // uniform over the CTA
+    base = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
+#pragma unroll
+    for (int q = 0; q < NV; q++)
+      v[q] = ok ? *reinterpret_cast<const float4 *>(a + base + offset(q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+
+  uint32_t ph0 = 0, ph1 = 0;   // parity each buffer's barrier waits for next
+  bool aborted = false;
+  bool prev = false;           // a tile of the previous iteration awaits its epilogue
+  uint64_t prev_base = 0;
+  float prev_nin = 0.f;
+  int it = 0;
+  long long tile = blockIdx.x;
+  gather(tile);
+  for (;; tile += gridDim.x, it++) {
+    const bool have = tile < p.n_tiles;
+    const int buf = it & 1;
+    uint64_t cur_base = 0;
+    float cur_nin = 0.f;
+    if (have) {
+      exchange(v, std::integral_constant<int, NV>{});
+      float mx = 0.f, nin = 0.f;
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+        nin = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, nin))));
+      }
+      red_in[2 * tid] = mx;
+      red_in[2 * tid + 1] = nin;
+      __syncthreads();
+      mx = fmaxf(mx, red_in[2 * (tid ^ kTcThreads)]);
+      nin += red_in[2 * (tid ^ kTcThreads) + 1];
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      const float sc = ldexpf(1.f, -e);
+      unsigned char *sA_hi = smem + (uint32_t)buf * 2u * A_BYTES;
+      unsigned char *sA_lo = sA_hi + A_BYTES;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
+                            v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
+        uint4 hi, lo;
+        uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+          const float2 hf = __half22float2(hh);
+          hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
+          lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
+        }
+        *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
+        *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+        const uint32_t dcol = tmem + (uint32_t)buf * (2 * KR);
+#pragma unroll
+        for (int ks = 0; ks < KR / 16; ks++) {
+          const uint32_t koff = (uint32_t)ks * 2u * LBO;
+          const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+          const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+          const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+          const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+          const uint32_t acc = ks > 0 ? 1u : 0u;
+          mma_f16(dcol, dah, dbh, IDESC, acc);
+          mma_f16(dcol + KR, dah, dbl, IDESC, acc);
+          mma_f16(dcol + KR, dal, dbh, IDESC, 1u);
+        }
+        if (!p.withhold_commit) mma_commit(smem_addr(&mbar[buf]));
+      }
+      cur_base = base;
+      cur_nin = nin;
+      gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
+    }
+    if (prev) {
+      // the previous tile (other buffer): wait for its MMAs, store it
+      const int pb = buf ^ 1;
+      const bool ok = mbar_wait(smem_addr(&mbar[pb]), pb ? ph1 : ph0);
+      if (pb) ph1 ^= 1;
+      else ph0 ^= 1;
+      if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        aborted = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t cb = lane_base + (uint32_t)pb * (2 * KR) + 64u * h;
+      float nout = 0.f;
+#pragma unroll
+      for (int hh = 0; hh < 4; hh++) {
+        uint32_t rb[16], rs[16];
+        TmemLd<16>::run(cb + 16 * hh, rb);
+        TmemLd<16>::run(cb + KR + 16 * hh, rs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+          const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+          nout = fmaf(y, y, nout);
+        }
+      }
+      red_out[tid] = nout;
+      __syncthreads();
+      nout += red_out[tid ^ kTcThreads];
+      const float f = nout > 0.f ? sqrtf(prev_nin / nout) : 1.f;
+#pragma unroll
+      for (int hh = 0; hh < 4; hh++) {
+        uint32_t rb[16], rs[16];
+        TmemLd<16>::run(cb + 16 * hh, rb);
+        TmemLd<16>::run(cb + KR + 16 * hh, rs);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        float4 y[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
+                             (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
+                             (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
+                             (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
+        exchange(y, std::integral_constant<int, 4>{});
+#pragma unroll
+        for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + prev_base + offset(4 * hh + q)) = y[q];
+      }
+    }
+    if (!have) break;
+    prev = true;
+    prev_base = cur_base;
+    prev_nin = cur_nin;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) {
+    // MMAs may still be in flight: one more commit tracks all of them; wait
+    // for it (bounded) before the columns are returned
+    if (tid == 0) mma_commit(smem_addr(&mbar[2]));
+    mbar_wait(smem_addr(&mbar[2]), 0);
   }
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
@@ -1016,6 +1273,38 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
   return cudaGetLastError();
 }
 
+cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                       cudaStream_t s) {
+  TcXParam p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_tiles = (1ll << (n - 6 - b.nctrl)) / kTcThreads;
+  p.cmask = b.cmask;
+  p.nf = x.nf;
+  for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
+  for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
+  for (int j = 0; j < 4; j++) p.rbit[j] = x.rbit[j];
+  p.la = x.la;
+  p.nswb = x.nswb;
+  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
+  p.th = x.th;
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
+  // two A buffers (hi + lo) of 64 KB and B (hi + lo) of 64 KB
+  const size_t smem = 4 * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
+  static thread_local int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (resident_ctas((const void *)k_dense_tc16x6, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms;  // one CTA per SM (512 TMEM columns each)
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16x6<<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t tc16_b_bytes(int k) { return 2u * (size_t)(2 << k) * (size_t)(2 << k) * 2u; }
@@ -1069,6 +1358,7 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     // B was built in slot order: no other kernel can take this block
     TcXLayout x;
     if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
+    if (b.k == 6) return run_tc16x6(a, n, b, x, dev_b, err, s);
     return b.k == 4 ? run_tc16x<4>(a, n, b, x, dev_b, err, s) : run_tc16x<5>(a, n, b, x, dev_b, err, s);
   }
   if (b.tc_staged && (b.k == 4 || b.k == 5)) {
@@ -1116,6 +1406,21 @@ bool tc_exchange_pays(const Block &b) {
 }
 
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
+  if (b.kind == BK_DENSE && b.k == 6 && !(b.cmask & 1ull)) {
+    // two threads per group: each half is a 5-target exchange over the five
+    // lower targets with the highest one fixed (like a control) per half
+    Block b5;
+    b5.kind = BK_DENSE;
+    b5.k = 5;
+    for (int j = 0; j < 5; j++) b5.q[j] = b.q[j];
+    b5.cmask = b.cmask | (1ull << b.q[5]);
+    b5.nctrl = b.nctrl + 1;
+    if (!tc_exchange_layout(n, b5, x)) return false;
+    x.th = b.q[5];
+    x.slot_mat[5] = 5;
+    return true;
+  }
+  x.th = -1;
   if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5) || (b.cmask & 1ull)) return false;
   const int K = b.k;
   if (n - K - b.nctrl < 7) return false;  // whole tiles of 128 groups

@@ -5,10 +5,10 @@ the planner's records against."""
 
 def lane_exchange_expected(n, qubits, ctrls):
     """(layout admits the lane exchange, the automatic rule picks it) for a
-    block with these targets and controls: bit 0 must not be a control and
-    the groups must fill tiles of 128; the automatic rule picks it for every
-    5-target block and for 4-target blocks with two or more targets among
-    bits 1..3."""
+    block with these targets and controls (4..6 of them): bit 0 must not be
+    a control and the groups must fill tiles of 128; the automatic rule picks
+    it for every 5-target block and for 4-target blocks with two or more
+    targets among bits 1..3."""
     fits = 0 not in ctrls and n - len(qubits) - len(ctrls) >= 7
-    pays = len(qubits) == 5 or len(set(qubits) & {1, 2, 3}) >= 2
+    pays = len(qubits) == 5 or (len(qubits) == 4 and len(set(qubits) & {1, 2, 3}) >= 2)
     return fits, pays

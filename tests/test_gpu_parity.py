@@ -164,10 +164,11 @@ def test_tc_threads_per_group(n, k, rows, gather, split):
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("ctrl", [None, 5, 0])
-@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n", [12, 17])
 def test_tc_lane_exchange(n, k, ctrl, mode):
-    """4- and 5-target tensor-core blocks with lane-exchange gathers
+    """4-, 5- and 6-target (two threads per group, double-buffered)
+    tensor-core blocks with lane-exchange gathers
     (opts.tc_exchange: 0 automatic, 1 never, 2 wherever the layout allows)
     on low-bit target patterns (no exchange, the element bit's exchange, one
     or two lane/register exchanges, targets moved from lane to register bits
@@ -185,8 +186,9 @@ def test_tc_lane_exchange(n, k, ctrl, mode):
                 [0, 1, 2, 3, 4], [1, 2, 3, 4, 5])
     kinds = set()
     for pattern in patterns:
-        qubits = pattern[:k]
-        if ctrl is not None and ctrl in qubits:
+        # 6 targets: the pattern plus the lowest qubit above it
+        qubits = pattern[:k] if k <= 5 else pattern + [max(pattern) + 1]
+        if ctrl is not None and ctrl in qubits or max(qubits) >= n:
             continue
         ctrls = [] if ctrl is None else [ctrl]
         if ctrl is None:
@@ -445,25 +447,32 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-def test_bounded_wait_times_out_and_state_recovers():
+@pytest.mark.parametrize("k,exchange", [(5, 0), (5, 1), (6, 2), (6, 1)])
+def test_bounded_wait_times_out_and_state_recovers(k, exchange):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
     frees its TMEM and returns, and the next synchronising call reports
-    QS_ETIMEOUT. The state stays usable."""
+    QS_ETIMEOUT. The state stays usable. Lane-exchange kernels (5 targets,
+    6 targets double-buffered) and the thread-per-group ones."""
     n = 14
-    gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(5)] + [("cx", [0, 1]), ("cx", [2, 3]), ("cx", [3, 4])]
+    gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(k)] + [("cx", [q, q + 1]) for q in range(0, k - 1, 2)]
+    gates += [("cx", [k - 2, k - 1])]
     arr = qs.gates_to_array(gates)
     st = qs.qs_alloc_state(n, qs.QS_C64)
     try:
         opts = qs.qs_default_opts()
         opts.test_wait_timeout = 1
-        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_TC, opts)
+        opts.tc_exchange = exchange
+        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC, opts)
+        _, recs = qs.qs_profile(st)
+        assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [1 if exchange == 1 else 2]
         with pytest.raises(qs.QsError) as e:
             qs.qs_norm(st)
         assert e.value.status == qs.QS_ETIMEOUT
         # the error is reported once; the state can be reset and used again
+        opts.test_wait_timeout = 0
         qs.qs_set_basis(st, 0)
-        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_TC)
+        qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC, opts)
         want, _ = oracle.simulate(cg.to_qasm(n, gates))
         got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
         assert np.linalg.norm(got - want) < 1e-5

@@ -262,7 +262,7 @@ def test_rules_select_follows_the_paper_rules():
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_lane_exchange_choice_on_benchmark_circuits(mode):
-    """The planner marks a 4/5-target tensor-core block for lane-exchange
+    """The planner marks a 4/5/6-target tensor-core block for lane-exchange
     gathers (record tc = 2) exactly where the rule says: automatic mode where
     the plain gather reads short runs, never with mode 1, wherever the layout
     fits with mode 2. Checked on every block of the n = 30 benchmark circuits
@@ -282,11 +282,11 @@ def test_lane_exchange_choice_on_benchmark_circuits(mode):
         cases.append((n, gates))
     seen = {1: 0, 2: 0}
     for n, gates in cases:
-        for k in (4, 5):
+        for k in (4, 5, 6):
             recs, _, _ = qs.qs_plan(n, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC,
                                     opts=o)
             for r in recs:
-                if r.kind != 0 or r.k not in (4, 5):
+                if r.kind != 0 or r.k not in (4, 5, 6):
                     continue
                 qubits = [int(x) for x in r.qubits[:r.k]]
                 ctrls = [q for q in range(n) if (r.cmask >> q) & 1]
