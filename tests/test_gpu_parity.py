@@ -176,6 +176,8 @@ def test_tc_lane_exchange(n, k, ctrl, mode):
     with a control on bit 5 and with bit 0 a control (no exchange layout),
     one tile (n = 12) and many (n = 17), from a random state; the record's tc
     field says which kernel ran (2 = lane exchange)."""
+    if k == 6 and ctrl is not None:
+        pytest.skip("a controlled 6-target block needs 7 fused qubits")
     rng = cg.SplitMix64(1300 + 10 * k + n + (ctrl or 0))
     o = qs.qs_default_opts()
     o.tc_exchange = mode
