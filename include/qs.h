@@ -121,7 +121,9 @@ typedef struct {
                            memory in address order (4, 5 targets); 2 = per-thread gathers, next
                            tile gathered during the MMAs; 3 = per-thread gathers without that
                            prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
-                           2 at 6); 4 = per-thread gathers two tiles ahead (same threads) */
+                           2 at 6); 4 = per-thread gathers two tiles ahead (same threads; for
+                           6-target lane-exchange blocks: two tiles in flight through double-
+                           buffered operands and accumulators) */
   int fuse_lookahead;   /* fusion: where a gate could join several blocks or open a new one,
                            each choice is followed by this many gates of first-fit placement
                            and the one leaving the fewest blocks is taken; 0 = first fit

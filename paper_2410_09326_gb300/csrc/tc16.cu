@@ -614,6 +614,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
 // SM idled for the MMAs (about a fifth of a tile). Slot bit 5 = the highest
 // target; the row's scale and norms are combined over the two halves through
 // shared memory.
+template <bool DB>
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
@@ -629,8 +630,8 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after both buffers
-  unsigned char *sB = smem + 4 * A_BYTES;
+  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after the buffers
+  unsigned char *sB = smem + (DB ? 4 : 2) * A_BYTES;
   __shared__ __align__(8) uint64_t mbar[3];  // per buffer; [2] for the final drain
   __shared__ uint32_t tmem_slot;
   __shared__ float red_in[2 * NT];
@@ -724,6 +725,54 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   };
 
   uint32_t ph0 = 0, ph1 = 0;   // parity each buffer's barrier waits for next
+  // wait for the MMAs of the tile in buffer pb, store it; false: timed out
+  auto epilogue = [&](int pb, uint64_t pbase, float pnin) -> bool {
+    const bool ok = mbar_wait(smem_addr(&mbar[pb]), pb ? ph1 : ph0);
+    if (pb) ph1 ^= 1;
+    else ph0 ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      return false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t cb = lane_base + (uint32_t)pb * (2 * KR) + 64u * h;
+    float nout = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < 4; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(cb + 16 * hh, rb);
+      TmemLd<16>::run(cb + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    red_out[tid] = nout;
+    __syncthreads();
+    nout += red_out[tid ^ kTcThreads];
+    const float f = nout > 0.f ? sqrtf(pnin / nout) : 1.f;
+#pragma unroll
+    for (int hh = 0; hh < 4; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(cb + 16 * hh, rb);
+      TmemLd<16>::run(cb + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float4 y[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
+                           (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
+                           (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
+                           (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
+      exchange(y, std::integral_constant<int, 4>{});
+#pragma unroll
+      for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + pbase + offset(4 * hh + q)) = y[q];
+    }
+    return true;
+  };
+
   bool aborted = false;
   bool prev = false;           // a tile of the previous iteration awaits its epilogue
   uint64_t prev_base = 0;
@@ -733,7 +782,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   gather(tile);
   for (;; tile += gridDim.x, it++) {
     const bool have = tile < p.n_tiles;
-    const int buf = it & 1;
+    const int buf = DB ? (it & 1) : 0;
     uint64_t cur_base = 0;
     float cur_nin = 0.f;
     if (have) {
@@ -795,52 +844,18 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       cur_nin = nin;
       gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
     }
-    if (prev) {
-      // the previous tile (other buffer): wait for its MMAs, store it
-      const int pb = buf ^ 1;
-      const bool ok = mbar_wait(smem_addr(&mbar[pb]), pb ? ph1 : ph0);
-      if (pb) ph1 ^= 1;
-      else ph0 ^= 1;
-      if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicExch(err, 1);
+    if (DB && prev) {
+      // the previous tile (other buffer) while this one's MMAs run
+      if (!epilogue(buf ^ 1, prev_base, prev_nin)) {
         aborted = true;
         break;
       }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t cb = lane_base + (uint32_t)pb * (2 * KR) + 64u * h;
-      float nout = 0.f;
-#pragma unroll
-      for (int hh = 0; hh < 4; hh++) {
-        uint32_t rb[16], rs[16];
-        TmemLd<16>::run(cb + 16 * hh, rb);
-        TmemLd<16>::run(cb + KR + 16 * hh, rs);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-        for (int i = 0; i < 16; i++) {
-          const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
-          nout = fmaf(y, y, nout);
-        }
-      }
-      red_out[tid] = nout;
-      __syncthreads();
-      nout += red_out[tid ^ kTcThreads];
-      const float f = nout > 0.f ? sqrtf(prev_nin / nout) : 1.f;
-#pragma unroll
-      for (int hh = 0; hh < 4; hh++) {
-        uint32_t rb[16], rs[16];
-        TmemLd<16>::run(cb + 16 * hh, rb);
-        TmemLd<16>::run(cb + KR + 16 * hh, rs);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        float4 y[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-          y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
-                             (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
-                             (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
-                             (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
-        exchange(y, std::integral_constant<int, 4>{});
-#pragma unroll
-        for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + prev_base + offset(4 * hh + q)) = y[q];
+    }
+    if (!DB && have) {
+      // single buffer: this tile, while the next one's loads are in flight
+      if (!epilogue(buf, cur_base, cur_nin)) {
+        aborted = true;
+        break;
       }
     }
     if (!have) break;
@@ -1273,6 +1288,7 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
   return cudaGetLastError();
 }
 
+template <bool DB>
 cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
                        cudaStream_t s) {
   TcXParam p;
@@ -1288,20 +1304,20 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
   for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
   p.th = x.th;
   p.withhold_commit = b.withhold_commit ? 1 : 0;
-  // two A buffers (hi + lo) of 64 KB and B (hi + lo) of 64 KB
-  const size_t smem = 4 * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
+  // one or two A buffers (hi + lo) of 64 KB and B (hi + lo) of 64 KB
+  const size_t smem = (DB ? 4 : 2) * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
   static thread_local int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6<DB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (resident_ctas((const void *)k_dense_tc16x6, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    if (resident_ctas((const void *)k_dense_tc16x6<DB>, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms;  // one CTA per SM (512 TMEM columns each)
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16x6<<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16x6<DB><<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -1358,7 +1374,8 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     // B was built in slot order: no other kernel can take this block
     TcXLayout x;
     if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
-    if (b.k == 6) return run_tc16x6(a, n, b, x, dev_b, err, s);
+    if (b.k == 6) return b.tc_prefetch == 2 ? run_tc16x6<true>(a, n, b, x, dev_b, err, s)
+                                            : run_tc16x6<false>(a, n, b, x, dev_b, err, s);
     return b.k == 4 ? run_tc16x<4>(a, n, b, x, dev_b, err, s) : run_tc16x<5>(a, n, b, x, dev_b, err, s);
   }
   if (b.tc_staged && (b.k == 4 || b.k == 5)) {

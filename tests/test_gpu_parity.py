@@ -162,6 +162,35 @@ def test_tc_threads_per_group(n, k, rows, gather, split):
         assert np.linalg.norm(got - want) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [17, 19])
+def test_tc6_lane_exchange_double_buffered(n):
+    """The 6-target lane-exchange kernel with two tiles in flight
+    (opts.tc_gather = 4: double-buffered A operands and TMEM accumulators)
+    on low and high target patterns, from a random state."""
+    rng = cg.SplitMix64(1700 + n)
+    o = qs.qs_default_opts()
+    o.tc_exchange = 2
+    o.tc_gather = 4
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    for qubits in ([0, 1, 2, 3, 4, 5], [1, 2, 8, 9, 10, 11], [7, 8, 9, 10, 11, 12], [0, 3, 9, 12, 14, 16]):
+        gates = []
+        for _ in range(2):
+            gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+            gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(6) | qs.QS_TC, o)
+            _, recs = qs.qs_profile(st)
+            assert [r.tc for r in recs if r.kind == 0 and r.k == 6] == [2]
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5, qubits
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("ctrl", [None, 5, 0])
 @pytest.mark.parametrize("k", [4, 5, 6])
@@ -449,13 +478,13 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("k,exchange", [(5, 0), (5, 1), (6, 2), (6, 1)])
-def test_bounded_wait_times_out_and_state_recovers(k, exchange):
+@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
+def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
     frees its TMEM and returns, and the next synchronising call reports
     QS_ETIMEOUT. The state stays usable. Lane-exchange kernels (5 targets,
-    6 targets double-buffered) and the thread-per-group ones."""
+    6 targets single- and double-buffered) and the thread-per-group ones."""
     n = 14
     gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(k)] + [("cx", [q, q + 1]) for q in range(0, k - 1, 2)]
     gates += [("cx", [k - 2, k - 1])]
@@ -465,6 +494,7 @@ def test_bounded_wait_times_out_and_state_recovers(k, exchange):
         opts = qs.qs_default_opts()
         opts.test_wait_timeout = 1
         opts.tc_exchange = exchange
+        opts.tc_gather = gather
         qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC, opts)
         _, recs = qs.qs_profile(st)
         assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [1 if exchange == 1 else 2]
