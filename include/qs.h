@@ -132,9 +132,10 @@ typedef struct {
                            the thread-per-group kernel instead of warp-wide loads and shuffles (c64) */
   int tc_split_k;       /* 6-target tensor-core blocks: 1 = K in two halves through 96 KB of shared
                            memory (two CTAs per SM), 2 = whole K (128 KB, one CTA); 0 = default */
-  int tc_exchange;      /* 4- and 5-target tensor-core blocks (FP16 halves, one thread per group):
+  int tc_exchange;      /* 4- to 6-target tensor-core blocks (FP16 halves):
                            0 = lane-exchange gathers where they measured faster (every 5-target
-                           block, 4-target blocks with two or more targets among bits 1..3);
+                           block, 4-target blocks with two or more targets among bits 1..3,
+                           6-target blocks (two threads per group) with one or more);
                            1 = never; 2 = wherever the layout allows (bit 0 not a control,
                            whole tiles of 128 groups) */
 } qs_opts;

@@ -109,7 +109,7 @@ struct TcXLayout {
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x);
 // True where the exchange kernel measured faster than the plain
 // thread-per-group gather: every 5-target block, 4-target blocks with two
-// or more targets among bits 1..3.
+// or more targets among bits 1..3, 6-target blocks with one or more.
 bool tc_exchange_pays(const Block &b);
 
 // Index of the pair (j, l), j < l < w, in a row-order upper triangle.

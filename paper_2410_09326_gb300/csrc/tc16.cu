@@ -603,17 +603,19 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-// Six targets: the same lane exchange, two threads per group and two tiles in
-// flight. Thread (h, r), h = tid / 128, holds the 32 amplitudes of group r
-// whose highest target equals h: warp w and warp w + 4 load the same 32
-// groups' two halves, each exactly as a 5-target exchange warp (the highest
-// target fixed per half). The A operands (64 KB per tile) and the TMEM
-// accumulators (256 columns per tile) are double-buffered, so the MMAs of
-// tile i run while the CTA stores tile i - 1 and gathers tile i + 1: with the
-// 6-target operands one CTA fills an SM, and without the second buffer the
-// SM idled for the MMAs (about a fifth of a tile). Slot bit 5 = the highest
-// target; the row's scale and norms are combined over the two halves through
-// shared memory.
+// Six targets: the same lane exchange with two threads per group. Thread
+// (h, r), h = tid / 128, holds the 32 amplitudes of group r whose highest
+// target equals h: warp w and warp w + 4 load the same 32 groups' two halves,
+// each exactly as a 5-target exchange warp (the highest target fixed per
+// half; slot bit 5 = the highest target). The row's scale and norms are
+// combined over the two halves through shared memory. The 6-target operands
+// fill an SM with one CTA, which idles while its MMAs run (about a fifth of
+// a tile); DB = true double-buffers the A operands (64 KB per tile) and the
+// TMEM accumulators (256 columns per tile) so that the MMAs of tile i run
+// while the CTA stores tile i - 1. Measured on GB300 that is slower (4.08-4.63
+// vs 4.40-5.51 TB/s): the next tile's loads then have only the stores to
+// arrive in, instead of the MMAs and the stores, and one CTA cannot hide the
+// rest of their latency. DB = false keeps the order of the other kernels.
 template <bool DB>
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
@@ -1415,11 +1417,13 @@ bool tc_exchange_pays(const Block &b) {
   // with at most one low target, 4.87-5.79 vs 3.21-4.96 with two or three);
   // with 4 targets only where two or more targets lie among bits 1..3
   // (4.89-5.34 vs 3.41-5.29 TB/s), elsewhere the plain gather is ahead
-  // (5.84-6.29 vs 5.59-5.87)
+  // (5.84-6.29 vs 5.59-5.87); with 6 targets (two threads per group) where
+  // any target lies among bits 1..3 (4.40-5.13 vs 3.17-5.02 TB/s), not for
+  // high targets (5.10-5.51 vs 5.50-5.54)
   if (b.k == 5) return true;
   int low = 0;
   for (int j = 0; j < b.k; j++) low += (b.q[j] >= 1 && b.q[j] <= 3) ? 1 : 0;
-  return low >= 2;
+  return b.k == 6 ? low >= 1 : low >= 2;
 }
 
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {

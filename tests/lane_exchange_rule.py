@@ -7,8 +7,9 @@ def lane_exchange_expected(n, qubits, ctrls):
     """(layout admits the lane exchange, the automatic rule picks it) for a
     block with these targets and controls (4..6 of them): bit 0 must not be
     a control and the groups must fill tiles of 128; the automatic rule picks
-    it for every 5-target block and for 4-target blocks with two or more
-    targets among bits 1..3."""
+    it for every 5-target block, for 4-target blocks with two or more
+    targets among bits 1..3 and for 6-target blocks with one or more."""
     fits = 0 not in ctrls and n - len(qubits) - len(ctrls) >= 7
-    pays = len(qubits) == 5 or (len(qubits) == 4 and len(set(qubits) & {1, 2, 3}) >= 2)
+    low = len(set(qubits) & {1, 2, 3})
+    pays = {4: low >= 2, 5: True, 6: low >= 1}[len(qubits)]
     return fits, pays
