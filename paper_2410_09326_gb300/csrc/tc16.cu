@@ -1411,7 +1411,7 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
 }  // namespace kern
 
 bool tc_exchange_pays(const Block &b) {
-  if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5)) return false;
+  if (b.kind != BK_DENSE || b.k < 4 || b.k > 6) return false;
   // measured on GB300 from random states at n = 28: with 5 targets the
   // exchange kernel is ahead for every placement (5.77-6.01 vs 5.56-5.72 TB/s
   // with at most one low target, 4.87-5.79 vs 3.21-4.96 with two or three);
