@@ -53,6 +53,19 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// One 16-byte core-matrix row of A from four scaled complex amplitudes
+// (re, im interleaved): hi = fp16(x), lo = fp16(x - hi).
+__device__ __forceinline__ void split_row(const float (&x)[8], uint4 &hi, uint4 &lo) {
+  uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
+    const float2 hf = __half22float2(hh);
+    hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
+    lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
+  }
+}
+
 // Resident CTAs per SM the register budget is sized for (TPR threads per row).
 // PFD = tiles gathered ahead into registers (0, 1 or 2). Without the
 // prefetch a thread needs fewer registers, so more CTAs fit and they hide
@@ -202,14 +215,7 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
         x[2 * u + 1] = v[4 * cl + u].y * sc;
       }
       uint4 hi, lo;
-      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
-        const float2 hf = __half22float2(hh);
-        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
-        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
-      }
+      split_row(x, hi, lo);
       *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
       *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
     }
@@ -374,6 +380,57 @@ struct TcXParam {
   int withhold_commit;
 };
 
+// The exchanges of the lane-exchange kernels, on N consecutive 16-byte
+// registers starting at a multiple of 4 (register bits 0 and 1 of the pairs
+// lie inside any such run): first the element bit with lane bit la -- half
+// of every register crosses: lane bit 0 keeps the element-0 half and trades
+// its element-1 half for the partner's element-0 half, lane bit 1 the other
+// way round -- then lane bit lb[i] with register bit i (half of the
+// registers cross). Each is an involution on its own pair of bits and the
+// pairs are disjoint, so running them again restores the load layout.
+struct LaneExchange {
+  int la, nswb, lb0, lb1, lane;
+  __device__ __forceinline__ LaneExchange(const TcXParam &p, int lane_)
+      : la(p.la), nswb(p.nswb), lb0(p.lb[0]), lb1(p.lb[1]), lane(lane_) {}
+  template <int N> __device__ __forceinline__ void run(float4 *w) const {
+    if (la >= 0) {
+      const bool up = (lane >> la) & 1;
+      const unsigned m = 1u << la;
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        const float s0 = up ? w[q].x : w[q].z, s1 = up ? w[q].y : w[q].w;
+        const float r0 = __shfl_xor_sync(0xffffffffu, s0, m), r1 = __shfl_xor_sync(0xffffffffu, s1, m);
+        if (up) {
+          w[q].x = r0;
+          w[q].y = r1;
+        } else {
+          w[q].z = r0;
+          w[q].w = r1;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      if (i >= nswb) break;
+      const int lbi = i == 0 ? lb0 : lb1;
+      const bool up = (lane >> lbi) & 1;
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        if ((q >> i) & 1) continue;
+        const int q2 = q | (1 << i);
+        const float4 snd = up ? w[q] : w[q2];
+        float4 rcv;
+        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
+        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
+        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
+        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
+        if (up) w[q] = rcv;
+        else w[q2] = rcv;
+      }
+    }
+  }
+};
+
 // Resident CTAs per SM of the exchange kernel (registers per thread follow).
 // Measured on GB300 from random states at n = 28: spill-free registers beat
 // more resident CTAs -- 5 targets at 2 CTAs (237 registers) ran 5413-6024
@@ -441,49 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
       if ((rr >> j) & 1) o += roff[j];
     return o;
   };
-  const int la = p.la, nswb = p.nswb;
-  const bool up_a = la >= 0 && ((lane >> (la & 31)) & 1);
-  const unsigned ma = 1u << (la & 31);
-  // the exchanges, on N consecutive registers starting at a multiple of 4
-  // (register bits 0 and 1 of the pairs lie inside any such run)
-  auto exchange = [&](float4 *w, auto n_regs) {
-    constexpr int N = decltype(n_regs)::value;
-    if (la >= 0) {
-#pragma unroll
-      for (int r = 0; r < N; r++) {
-        // lane bit 0 keeps the element-0 half and trades its element-1 half
-        // for the partner's element-0 half; lane bit 1 the other way round
-        const float s0 = up_a ? w[r].x : w[r].z, s1 = up_a ? w[r].y : w[r].w;
-        const float r0 = __shfl_xor_sync(0xffffffffu, s0, ma), r1 = __shfl_xor_sync(0xffffffffu, s1, ma);
-        if (up_a) {
-          w[r].x = r0;
-          w[r].y = r1;
-        } else {
-          w[r].z = r0;
-          w[r].w = r1;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-      if (i >= nswb) break;
-      const int lbi = p.lb[i];
-      const bool up = (lane >> lbi) & 1;
-#pragma unroll
-      for (int r = 0; r < N; r++) {
-        if ((r >> i) & 1) continue;
-        const int r2 = r | (1 << i);
-        const float4 snd = up ? w[r] : w[r2];
-        float4 rcv;
-        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
-        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
-        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
-        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
-        if (up) w[r] = rcv;
-        else w[r2] = rcv;
-      }
-    }
-  };
+  const LaneExchange xch(p, lane);
 
   uint32_t phase = 0;
   bool aborted = false;
@@ -501,7 +516,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
   gather(tile);
 
   for (; tile < p.n_tiles; tile += gridDim.x) {
-    exchange(v, std::integral_constant<int, NV>{});
+    xch.run<NV>(v);
     float mx = 0.f, nin = 0.f;
 #pragma unroll
     for (int r = 0; r < NV; r++) {
@@ -517,14 +532,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
       const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
                           v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
       uint4 hi, lo;
-      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
-        const float2 hf = __half22float2(hh);
-        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
-        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
-      }
+      split_row(x, hi, lo);
       *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
       *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
     }
@@ -587,7 +595,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
                            (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
                            (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
                            (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
-      exchange(y, std::integral_constant<int, 4>{});
+      xch.run<4>(y);
       if (cur_valid) {
 #pragma unroll
         for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
@@ -676,45 +684,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       if ((rr >> j) & 1) o += roff[j];
     return o;
   };
-  const int la = p.la, nswb = p.nswb;
-  const bool up_a = la >= 0 && ((lane >> (la & 31)) & 1);
-  const unsigned ma = 1u << (la & 31);
-  auto exchange = [&](float4 *w, auto n_regs) {
-    constexpr int N = decltype(n_regs)::value;
-    if (la >= 0) {
-#pragma unroll
-      for (int q = 0; q < N; q++) {
-        const float s0 = up_a ? w[q].x : w[q].z, s1 = up_a ? w[q].y : w[q].w;
-        const float r0 = __shfl_xor_sync(0xffffffffu, s0, ma), r1 = __shfl_xor_sync(0xffffffffu, s1, ma);
-        if (up_a) {
-          w[q].x = r0;
-          w[q].y = r1;
-        } else {
-          w[q].z = r0;
-          w[q].w = r1;
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-      if (i >= nswb) break;
-      const int lbi = p.lb[i];
-      const bool up = (lane >> lbi) & 1;
-#pragma unroll
-      for (int q = 0; q < N; q++) {
-        if ((q >> i) & 1) continue;
-        const int q2 = q | (1 << i);
-        const float4 snd = up ? w[q] : w[q2];
-        float4 rcv;
-        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
-        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
-        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
-        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
-        if (up) w[q] = rcv;
-        else w[q2] = rcv;
-      }
-    }
-  };
+  const LaneExchange xch(p, lane);
 
   float4 v[NV];
   uint64_t base = 0;
@@ -768,7 +738,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
                            (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
                            (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
                            (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
-      exchange(y, std::integral_constant<int, 4>{});
+      xch.run<4>(y);
 #pragma unroll
       for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + pbase + offset(4 * hh + q)) = y[q];
     }
@@ -788,7 +758,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     uint64_t cur_base = 0;
     float cur_nin = 0.f;
     if (have) {
-      exchange(v, std::integral_constant<int, NV>{});
+      xch.run<NV>(v);
       float mx = 0.f, nin = 0.f;
 #pragma unroll
       for (int q = 0; q < NV; q++) {
@@ -810,14 +780,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
         const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
                             v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
         uint4 hi, lo;
-        uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
-          const float2 hf = __half22float2(hh);
-          hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
-          lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
-        }
+        split_row(x, hi, lo);
         *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
         *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
       }
@@ -1036,14 +999,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         x[2 * u + 1] = v[4 * c + u].y * sc;
       }
       uint4 hi, lo;
-      uint32_t *hp = reinterpret_cast<uint32_t *>(&hi), *lp = reinterpret_cast<uint32_t *>(&lo);
-#pragma unroll
-      for (int u = 0; u < 4; u++) {
-        const __half2 hh = __floats2half2_rn(x[2 * u], x[2 * u + 1]);
-        const float2 hf = __half22float2(hh);
-        hp[u] = *reinterpret_cast<const uint32_t *>(&hh);
-        lp[u] = pack_half2(x[2 * u] - hf.x, x[2 * u + 1] - hf.y);
-      }
+      split_row(x, hi, lo);
       *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
       *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
     }
