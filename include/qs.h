@@ -301,6 +301,48 @@ qs_status qs_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags, c
                   double *mats, size_t mats_cap, size_t *mats_len);
 
 /*
+ * Device-memory budget for the library's own allocations (states from
+ * qs_alloc_state, reduction and matrix scratch, batch plans, cost-model
+ * buffers; borrowed states do not count). 0 = no budget (the default). An
+ * allocation that would take the library's live device bytes above the
+ * budget fails with QS_ENOMEM before any CUDA call; lowering the budget
+ * frees nothing. Process wide and thread-safe. qs_memory_in_use returns the
+ * library's live device bytes.
+ */
+void qs_set_memory_limit(uint64_t bytes);
+uint64_t qs_memory_in_use(void);
+
+/*
+ * Lane-exchange layout of the FP16 tensor-core kernels (introspection for
+ * tests and tools; host only, no GPU). A warp of those kernels owns the
+ * sub-cube spanned by a block's targets and its five lowest free bits (6
+ * targets: the five lower targets, the highest one fixed per thread half),
+ * loads it with 16-byte accesses (element bit = bit 0) whose lane bits and
+ * register bits are given below, and exchanges bits between positions with
+ * warp shuffles until every lane holds one group: first the element bit with
+ * lane bit la (if la >= 0), then lane bit lb[i] with register bit i for
+ * i < nswb. Slot bit 0 is then the element bit, slot bit 1 + j register bit j
+ * (slot bit 5 = half_bit for 6 targets); slot_target[s] is the position, in
+ * the ascending target list, of the target slot bit s holds.
+ * targets: k (4..6) distinct ascending physical bits < n; cmask: controls,
+ * disjoint from them. Returns QS_EINVAL for bad arguments; *out->applies = 0
+ * when the block cannot take the layout (bit 0 a control, fewer than 7 free
+ * bits, too many fixed bits).
+ */
+typedef struct {
+  int32_t applies;
+  int32_t lane_bits[5];    /* physical bit of lane bit i, as loaded */
+  int32_t reg_bits[4];     /* physical bit of register bit j, as loaded (k - 1 used, 4 for k = 6) */
+  int32_t la;              /* lane bit exchanged with the element bit, -1 if none */
+  int32_t nswb;            /* lane/register exchanges (0..2) */
+  int32_t lb[2];           /* their lane bits */
+  int32_t slot_target[6];  /* slot bit -> index in the ascending target list */
+  int32_t half_bit;        /* 6 targets: physical bit fixed per thread half; else -1 */
+} qs_exchange_layout;
+
+qs_status qs_tc_exchange_layout(int n, int k, const int *targets, uint64_t cmask, qs_exchange_layout *out);
+
+/*
  * Rotation folding (Sec. III-D): phase rotations (T, T^dagger, S, S^dagger,
  * Z, U1, RZ) on the same parity of a CNOT/X/SWAP/diagonal region merge into
  * the first of them (e.g. T . T -> S), then adjacent equal self-inverse gates

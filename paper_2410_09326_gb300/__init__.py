@@ -90,6 +90,12 @@ class qs_block_record(ctypes.Structure):
                 ("t_start_ms", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
+class qs_exchange_layout(ctypes.Structure):
+    _fields_ = [("applies", ctypes.c_int32), ("lane_bits", ctypes.c_int32 * 5), ("reg_bits", ctypes.c_int32 * 4),
+                ("la", ctypes.c_int32), ("nswb", ctypes.c_int32), ("lb", ctypes.c_int32 * 2),
+                ("slot_target", ctypes.c_int32 * 6), ("half_bit", ctypes.c_int32)]
+
+
 class qs_profile_summary(ctypes.Structure):
     _fields_ = [("n_qubits", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
                 ("gates_seen", ctypes.c_int64), ("gates_last", ctypes.c_int32),
@@ -168,6 +174,10 @@ def load(build_if_missing=False):
                                           ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(qs_opts)]),
         "qs_probs_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.c_int, vp, vp]),
+        "qs_set_memory_limit": (None, [ctypes.c_uint64]),
+        "qs_memory_in_use": (ctypes.c_uint64, []),
+        "qs_tc_exchange_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.c_uint64, ctypes.POINTER(qs_exchange_layout)]),
         "qs_plan": (ctypes.c_int, [ctypes.c_int, vp, sz, ctypes.c_uint64, ctypes.POINTER(qs_opts),
                                    ctypes.POINTER(ctypes.c_int8), ctypes.POINTER(qs_block_record), sz,
                                    ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_double), sz,
@@ -353,6 +363,24 @@ def qs_device_ptr(st):
     p = ctypes.c_void_p()
     _check(load().qs_device_ptr(st, ctypes.byref(p)))
     return p.value
+
+
+def qs_set_memory_limit(nbytes):
+    """Device-memory budget for the library's own allocations (0 = none)."""
+    load().qs_set_memory_limit(int(nbytes))
+
+
+def qs_memory_in_use():
+    """The library's live device bytes."""
+    return int(load().qs_memory_in_use())
+
+
+def qs_tc_exchange_layout(n, targets, cmask=0):
+    """The lane-exchange layout of a tensor-core block (qs_exchange_layout)."""
+    t = (ctypes.c_int * len(targets))(*[int(x) for x in targets])
+    out = qs_exchange_layout()
+    _check(load().qs_tc_exchange_layout(n, len(targets), t, cmask, ctypes.byref(out)))
+    return out
 
 
 def qs_plan(n, gates, flags=QS_PLAIN, opts=None, perm=None):

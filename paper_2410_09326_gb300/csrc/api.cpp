@@ -159,10 +159,10 @@ struct DeviceGuard {
 
 template <typename T> cudaError_t grow(T *&ptr, size_t &cap, size_t need) {
   if (need <= cap) return cudaSuccess;
-  if (ptr) cudaFree(ptr);
+  dev_free(ptr);
   ptr = nullptr;
   cap = 0;
-  cudaError_t e = cudaMalloc((void **)&ptr, need * sizeof(T));
+  cudaError_t e = dev_malloc((void **)&ptr, need * sizeof(T));
   if (e == cudaSuccess) cap = need;
   return e;
 }
@@ -223,12 +223,13 @@ qs_status qs_alloc_state(int n, qs_dtype dtype, void *cuda_stream, qs_state **ou
   if (s != QS_OK) return s;
   qs_state *st = *out;
   const size_t bytes = (size_t)amp_bytes(st) << n;
-  cudaError_t e = cudaMalloc(&st->amps, bytes);
+  cudaError_t e = dev_malloc(&st->amps, bytes);
   if (e != cudaSuccess) {
-    cudaGetLastError();
     delete st;
     *out = nullptr;
-    return fail(QS_ENOMEM, std::string("cudaMalloc of the state failed: ") + cudaGetErrorString(e));
+    return fail(QS_ENOMEM, dev_refused_by_budget() ? std::string("state allocation refused by the memory budget")
+                                                   : std::string("device allocation of the state failed: ") +
+                                                         cudaGetErrorString(e));
   }
   st->owned = true;
   e = launch_set_basis(st->amps, n, dtype == QS_C128, 0, st->stream);
@@ -251,13 +252,13 @@ void qs_free_state(qs_state *st) {
   DeviceGuard g(st->device);
   if (st->stream) cudaStreamSynchronize(st->stream);
   else cudaDeviceSynchronize();
-  if (st->owned && st->amps) cudaFree(st->amps);
-  if (st->d_partial) cudaFree(st->d_partial);
-  if (st->d_out) cudaFree(st->d_out);
-  if (st->d_mats) cudaFree(st->d_mats);
+  if (st->owned) dev_free(st->amps);
+  dev_free(st->d_partial);
+  dev_free(st->d_out);
+  dev_free(st->d_mats);
   if (st->h_mats) cudaFreeHost(st->h_mats);
   if (st->mats_copied) cudaEventDestroy(st->mats_copied);
-  if (st->d_err) cudaFree(st->d_err);
+  dev_free(st->d_err);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
   delete st;
 }
@@ -348,10 +349,11 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
     size_t cap_bytes = st->mats_cap;
     unsigned char *dm = (unsigned char *)st->d_mats;
     if (mat_bytes > cap_bytes) {
-      if (dm) cudaFree(dm);
+      dev_free(dm);
       dm = nullptr;
+      st->d_mats = nullptr;
       st->mats_cap = 0;
-      e = cudaMalloc((void **)&dm, mat_bytes);
+      e = dev_malloc((void **)&dm, mat_bytes);
       if (e != cudaSuccess) return fail(QS_ENOMEM, "matrix buffer allocation failed");
       st->d_mats = dm;
       st->mats_cap = mat_bytes;
@@ -366,7 +368,7 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   }
 
   if (any_tc && !st->d_err) {
-    e = cudaMalloc((void **)&st->d_err, sizeof(int));
+    e = dev_malloc((void **)&st->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(st->d_err, 0, sizeof(int), st->stream);
     if (e != cudaSuccess) return fail(QS_ENOMEM, "error word allocation failed");
   }
@@ -506,6 +508,37 @@ qs_status qs_profile_reset(qs_state *st) {
   std::memset(st->max_run_1q, 0, sizeof(st->max_run_1q));
   st->gates_seen = 0;
   st->recs.clear();
+  return QS_OK;
+}
+
+qs_status qs_tc_exchange_layout(int n, int k, const int *targets, uint64_t cmask, qs_exchange_layout *out) {
+  if (!targets || !out) return fail(QS_EINVAL, "null argument");
+  if (n < 1 || n > QS_MAX_QUBITS || k < 4 || k > 6) return fail(QS_EINVAL, "n or k out of range");
+  Block b;
+  b.kind = BK_DENSE;
+  b.k = k;
+  uint64_t tmask = 0;
+  for (int j = 0; j < k; j++) {
+    if (targets[j] < 0 || targets[j] >= n || (j > 0 && targets[j] <= targets[j - 1]))
+      return fail(QS_EINVAL, "targets must be distinct, ascending and below n");
+    b.q[j] = targets[j];
+    tmask |= 1ull << targets[j];
+  }
+  if ((cmask & tmask) || (n < 64 && (cmask >> n))) return fail(QS_EINVAL, "bad control mask");
+  b.cmask = cmask;
+  b.nctrl = __builtin_popcountll(cmask);
+  std::memset(out, 0, sizeof(*out));
+  TcXLayout x;
+  if (!tc_exchange_layout(n, b, x)) return QS_OK;
+  out->applies = 1;
+  for (int i = 0; i < 5; i++) out->lane_bits[i] = x.lbit[i];
+  const int rb = k == 6 ? 4 : k - 1;
+  for (int j = 0; j < 4; j++) out->reg_bits[j] = j < rb ? x.rbit[j] : -1;
+  out->la = x.la;
+  out->nswb = x.nswb;
+  for (int i = 0; i < 2; i++) out->lb[i] = i < x.nswb ? x.lb[i] : -1;
+  for (int s = 0; s < 6; s++) out->slot_target[s] = s < k ? x.slot_mat[s] : -1;
+  out->half_bit = x.th;
   return QS_OK;
 }
 

@@ -193,10 +193,10 @@ qs_status bfail(qs_status s, const std::string &m) {
 }
 
 void free_plan(qs_batch *b) {
-  if (b->d_circs) cudaFree(b->d_circs);
-  if (b->d_order) cudaFree(b->d_order);
-  if (b->d_blocks) cudaFree(b->d_blocks);
-  if (b->d_pool) cudaFree(b->d_pool);
+  qs::dev_free(b->d_circs);
+  qs::dev_free(b->d_order);
+  qs::dev_free(b->d_blocks);
+  qs::dev_free(b->d_pool);
   b->d_circs = nullptr;
   b->d_order = nullptr;
   b->d_blocks = nullptr;
@@ -250,10 +250,10 @@ qs_status upload_plan(qs_batch *bt, uint64_t flags) {
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
   if (pool.empty()) pool.push_back(make_float2(0.f, 0.f));
   if (blocks.empty()) blocks.push_back(BBlock());
-  cudaError_t e = cudaMalloc((void **)&bt->d_circs, sizeof(BCircuit) * circs.size());
-  if (e == cudaSuccess) e = cudaMalloc((void **)&bt->d_order, sizeof(int) * order.size());
-  if (e == cudaSuccess) e = cudaMalloc((void **)&bt->d_blocks, sizeof(BBlock) * blocks.size());
-  if (e == cudaSuccess) e = cudaMalloc((void **)&bt->d_pool, sizeof(float2) * pool.size());
+  cudaError_t e = qs::dev_malloc((void **)&bt->d_circs, sizeof(BCircuit) * circs.size());
+  if (e == cudaSuccess) e = qs::dev_malloc((void **)&bt->d_order, sizeof(int) * order.size());
+  if (e == cudaSuccess) e = qs::dev_malloc((void **)&bt->d_blocks, sizeof(BBlock) * blocks.size());
+  if (e == cudaSuccess) e = qs::dev_malloc((void **)&bt->d_pool, sizeof(float2) * pool.size());
   if (e != cudaSuccess) return bfail(QS_ENOMEM, "qs_batch: descriptor allocation failed");
   e = cudaMemcpy(bt->d_circs, circs.data(), sizeof(BCircuit) * circs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(bt->d_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice);
@@ -325,7 +325,7 @@ qs_status qs_batch_create(qs_state *const *states, const qs_gate *const *gates, 
     e = cudaStreamCreateWithFlags(&bt->own_stream, cudaStreamDefault);  // ordered with the legacy stream
     bt->stream = bt->own_stream;
   }
-  if (e == cudaSuccess) e = cudaMalloc((void **)&bt->d_queue, sizeof(int));
+  if (e == cudaSuccess) e = qs::dev_malloc((void **)&bt->d_queue, sizeof(int));
   if (e != cudaSuccess) {
     qs_batch_free(bt);
     return bfail(QS_ECUDA, std::string("qs_batch_create: ") + cudaGetErrorString(e));
@@ -449,7 +449,7 @@ void qs_batch_free(qs_batch *bt) {
   if (bt->exec) cudaGraphExecDestroy(bt->exec);
   if (bt->graph) cudaGraphDestroy(bt->graph);
   free_plan(bt);
-  if (bt->d_queue) cudaFree(bt->d_queue);
+  qs::dev_free(bt->d_queue);
   if (bt->own_stream) cudaStreamDestroy(bt->own_stream);
   delete bt;
 }

@@ -140,9 +140,9 @@ qs_status mfail(qs_status s, const std::string &m) {
 }
 
 template <typename T> cudaError_t dalloc(T *&p, size_t n) {
-  if (p) cudaFree(p);
+  qs::dev_free(p);
   p = nullptr;
-  return cudaMalloc((void **)&p, sizeof(T) * (n ? n : 1));
+  return qs::dev_malloc((void **)&p, sizeof(T) * (n ? n : 1));
 }
 
 cudaError_t ensure_batch(qs_mlp *mm, int B) {
@@ -235,9 +235,8 @@ void qs_mlp_free(qs_mlp *mm) {
   cudaDeviceSynchronize();
   float *bufs[] = {mm->p, mm->g, mm->m, mm->v, mm->x, mm->t, mm->h1, mm->h2, mm->y, mm->dy, mm->dh2, mm->dh1,
                    mm->loss, mm->data_x, mm->data_y};
-  for (float *b : bufs)
-    if (b) cudaFree(b);
-  if (mm->idx) cudaFree(mm->idx);
+  for (float *b : bufs) qs::dev_free(b);
+  qs::dev_free(mm->idx);
   delete mm;
 }
 

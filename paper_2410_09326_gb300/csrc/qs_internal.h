@@ -160,6 +160,13 @@ qs_status measured_select(int n, bool c128, const qs_gate *gates, size_t n_gates
 qs_status mlp_select(qs_mlp *mm, int n, bool c128, const qs_gate *gates, size_t n_gates, const qs_opts &o,
                      uint64_t *flags_out, double *pred_ms, std::string &err);
 
+// Device allocations counted against the budget of qs_set_memory_limit
+// (devmem.cpp); dev_free takes null.
+cudaError_t dev_malloc(void **p, size_t bytes);
+void dev_free(void *p);
+// True when this thread's last dev_malloc was refused by the budget.
+bool dev_refused_by_budget();
+
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels.cu). All asynchronous on `s`.
 // ---------------------------------------------------------------------------

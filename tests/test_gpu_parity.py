@@ -512,6 +512,36 @@ def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
         qs.qs_free_state(st)
 
 
+def test_memory_budget_on_device():
+    """The device-memory budget counts the state and the scratch the library
+    allocates: with room for the state only, a 6-qubit block (its matrix goes
+    through a device buffer) is refused with QS_ENOMEM before anything runs;
+    without the budget the same call runs and matches the oracle; freeing the
+    state returns the live byte count to where it was."""
+    n = 16
+    base = qs.qs_memory_in_use()
+    qs.qs_set_memory_limit(base + (8 << n) + 4096)
+    gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(6)] + [("cx", [q, q + 1]) for q in range(5)]
+    arr = qs.gates_to_array(gates)
+    try:
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            assert qs.qs_memory_in_use() == base + (8 << n)
+            with pytest.raises(qs.QsError) as e:
+                qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(6))
+            assert e.value.status == qs.QS_ENOMEM
+            qs.qs_set_memory_limit(0)
+            qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(6))
+            want, _ = oracle.simulate(cg.to_qasm(n, gates))
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+            assert np.linalg.norm(got - want) < 1e-5
+        finally:
+            qs.qs_free_state(st)
+        assert qs.qs_memory_in_use() == base
+    finally:
+        qs.qs_set_memory_limit(0)
+
+
 def test_attach_torch_tensor_and_stream():
     torch = pytest.importorskip("torch")
     n = 12

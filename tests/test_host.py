@@ -260,6 +260,120 @@ def test_rules_select_follows_the_paper_rules():
     assert len(recs) < len(gates) // 2  # and gates were merged
 
 
+def test_memory_budget_refuses_before_any_cuda_call():
+    """A state larger than the device-memory budget is refused with
+    QS_ENOMEM by the budget itself (no CUDA call is made, so this holds
+    without a GPU); the live byte count is unchanged."""
+    before = qs.qs_memory_in_use()
+    qs.qs_set_memory_limit(1 << 20)
+    try:
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_alloc_state(20, qs.QS_C64)  # 8 MiB
+        assert e.value.status == qs.QS_ENOMEM and "memory budget" in str(e.value)
+        assert qs.qs_memory_in_use() == before
+    finally:
+        qs.qs_set_memory_limit(0)
+
+
+def exchange_emulation(lay, k):
+    """Offsets (from the warp's base) of the amplitudes each lane of a
+    lane-exchange warp loads, as a (32 lanes, registers, 2 elements) array,
+    and the kernel's exchange step on such an array: the element bit with lane
+    bit la (the lane whose la bit is 1 takes the partner's element-1 half into
+    its element-0 half, the other lane the partner's element-0 half into its
+    element-1 half), then lane bit lb[i] with register bit i (the lane whose
+    lb bit is 1 takes the partner's register q2 = q | 2^i into its register q,
+    the other the partner's register q into its register q2)."""
+    nv = 16 if k == 6 else 1 << (k - 1)
+    nrb = 4 if k == 6 else k - 1
+    lanes = np.arange(32, dtype=np.int64)
+    regs = np.arange(nv, dtype=np.int64)
+    lane_off = sum(((lanes >> i) & 1) << int(lay.lane_bits[i]) for i in range(5))
+    reg_off = sum(((regs >> j) & 1) << int(lay.reg_bits[j]) for j in range(nrb))
+    off = lane_off[:, None, None] + reg_off[None, :, None] + np.arange(2, dtype=np.int64)[None, None, :]
+
+    def run(w):
+        w = w.copy()
+        n_regs = w.shape[1]
+        if lay.la >= 0:
+            up = ((lanes >> lay.la) & 1) == 1
+            partner = lanes ^ (1 << lay.la)
+            old = w.copy()
+            w[up, :, 0] = old[partner[up], :, 1]
+            w[~up, :, 1] = old[partner[~up], :, 0]
+        for i in range(lay.nswb):
+            up = ((lanes >> lay.lb[i]) & 1) == 1
+            partner = lanes ^ (1 << lay.lb[i])
+            old = w.copy()
+            for q in range(n_regs):
+                if (q >> i) & 1:
+                    continue
+                q2 = q | (1 << i)
+                w[up, q, :] = old[partner[up], q2, :]
+                w[~up, q2, :] = old[partner[~up], q, :]
+        return w
+
+    return off, run
+
+
+def test_lane_exchange_layout_index_arithmetic():
+    """The tensor-core lane-exchange layout (qs_tc_exchange_layout), checked
+    by emulating a warp on the CPU for 3000 random blocks (4..6 targets,
+    biased to low bits, 0..2 controls, n up to 34): the element, lane and
+    register bits are exactly the warp's sub-cube (targets + five lowest free
+    bits), so every amplitude of a sub-cube is loaded once; after the
+    exchanges every lane holds one group -- one assignment of the free bits
+    -- in slot order (slot bit s -> target slot_target[s]); the exchanges run
+    again 4 registers at a time (as the kernels' stores do) restore the load
+    layout; the layout applies exactly when bit 0 is not a control and 7 or
+    more free bits remain."""
+    rng = cg.SplitMix64(4242)
+    applied = 0
+    for _ in range(3000):
+        k = 4 + rng.randint(3)
+        nctrl = rng.randint(3)
+        n = min(34, k + nctrl + 5 + rng.randint(12))
+        chosen = []
+        while len(chosen) < k + nctrl:
+            q = rng.randint(n) if rng.randint(3) == 0 else rng.randint(min(n, 8))
+            if q not in chosen:
+                chosen.append(q)
+        targets = sorted(chosen[:k])
+        ctrls = chosen[k:]
+        cmask = sum(1 << c for c in ctrls)
+        lay = qs.qs_tc_exchange_layout(n, targets, cmask)
+        assert bool(lay.applies) == (0 not in ctrls and n - k - nctrl >= 7), (n, targets, ctrls)
+        if not lay.applies:
+            continue
+        applied += 1
+        inner = targets[:5]
+        free5 = [q for q in range(64) if q not in targets and q not in ctrls][:5]
+        cube = sorted(set(inner) | set(free5))
+        nrb = 4 if k == 6 else k - 1
+        pos = [0] + list(lay.lane_bits) + list(lay.reg_bits[:nrb])
+        assert sorted(pos) == cube, (targets, ctrls, pos, cube)
+        if k == 6:
+            assert lay.half_bit == targets[5] and lay.slot_target[5] == 5
+        else:
+            assert lay.half_bit == -1
+        assert 0 <= lay.nswb <= 2
+        off, run = exchange_emulation(lay, k)
+        after = run(off)
+        tmask = sum(1 << t for t in inner)
+        nv = off.shape[1]
+        rho = (np.arange(2)[None, :] + 2 * np.arange(nv)[:, None])   # slot of (register, element)
+        slot_off = np.zeros_like(rho)
+        for sb in range(min(k, 5)):
+            slot_off += ((rho >> sb) & 1) << targets[lay.slot_target[sb]]
+        groups = after[:, 0, 0]
+        assert np.all(groups & tmask == 0)
+        assert sorted(groups.tolist()) == sorted(sum(((g >> i) & 1) << free5[i] for i in range(5)) for g in range(32))
+        assert np.array_equal(after, groups[:, None, None] + slot_off[None, :, :])
+        back = np.concatenate([run(after[:, c:c + 4, :]) for c in range(0, nv, 4)], axis=1)
+        assert np.array_equal(back, off)
+    assert applied > 2000
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_lane_exchange_choice_on_benchmark_circuits(mode):
     """The planner marks a 4/5/6-target tensor-core block for lane-exchange
