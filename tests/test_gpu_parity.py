@@ -512,6 +512,29 @@ def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
         qs.qs_free_state(st)
 
 
+def test_chrome_trace_of_a_profiled_call(tmp_path):
+    """A profiled apply call (QS_PROFILE) exported as a Chrome trace: one
+    event per launched block, durations summing to the profile's device time,
+    starts in launch order."""
+    import json
+
+    from paper_2410_09326_gb300 import trace
+    n = 16
+    gates = cg.random_layered(n, 6, cg.SplitMix64(88), n_swaps=3)
+    st = qs.qs_alloc_state(n, qs.QS_C64)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_PGO_RULES | qs.QS_PROFILE)
+        summ, recs = qs.qs_profile(st)
+        path = tmp_path / "trace.json"
+        assert trace.write_chrome_trace(st, str(path)) == len(recs) > 0
+    finally:
+        qs.qs_free_state(st)
+    ev = json.loads(path.read_text())["traceEvents"]
+    assert abs(sum(e["dur"] for e in ev) / 1e3 - summ.total_ms) < 1e-6 * max(1.0, summ.total_ms)
+    starts = [e["ts"] for e in ev]
+    assert starts == sorted(starts)
+
+
 def test_memory_budget_on_device():
     """The device-memory budget counts the state and the scratch the library
     allocates: with room for the state only, a 6-qubit block (its matrix goes

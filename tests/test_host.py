@@ -8,6 +8,7 @@ is a valid answer as long as the product matches; no partition is assumed.
 """
 
 import ctypes
+import json
 import math
 import re
 import subprocess
@@ -258,6 +259,30 @@ def test_rules_select_follows_the_paper_rules():
     _, operm = oracle.simulate(cg.to_qasm(n, gates))
     assert list(perm) == list(operm)  # SWAPs were absorbed
     assert len(recs) < len(gates) // 2  # and gates were merged
+
+
+def test_chrome_trace_of_block_records():
+    """The Chrome-trace export: one complete event per timed record (start
+    and duration in microseconds, the kernel class as the name, qubits without
+    the -1 padding, GB/s from bytes and time), untimed records skipped, and
+    the result serialisable as JSON."""
+    from paper_2410_09326_gb300 import trace
+    recs = []
+    for i, (kind, k, tc, start, ms) in enumerate([(0, 5, 2, 0.0, 2.9), (4, 12, 0, 2.9, 2.8), (0, 3, 0, -1.0, -1.0)]):
+        r = qs.qs_block_record()
+        r.index, r.kind, r.k, r.tc, r.n_gates = i, kind, k, tc, 7
+        for j in range(len(r.qubits)):
+            r.qubits[j] = j if j < k else -1
+        r.bytes = 17179869184.0
+        r.t_start_ms, r.ms = start, ms
+        recs.append(r)
+    tr = json.loads(json.dumps(trace.chrome_trace(recs)))
+    ev = tr["traceEvents"]
+    assert len(ev) == 2 and all(e["ph"] == "X" for e in ev)
+    assert ev[0]["name"] == "dense k=5 tensor cores lane exchange" and ev[1]["name"] == "phase polynomial k=12"
+    assert ev[0]["ts"] == 0.0 and abs(ev[0]["dur"] - 2900.0) < 1e-9 and abs(ev[1]["ts"] - 2900.0) < 1e-9
+    assert ev[0]["args"]["qubits"] == [0, 1, 2, 3, 4] and ev[0]["args"]["gates"] == 7
+    assert abs(ev[0]["args"]["GB/s"] - 17179869184.0 / 2.9 / 1e6) < 1e-6
 
 
 def test_memory_budget_refuses_before_any_cuda_call():
