@@ -863,8 +863,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     TcXLayout xl;
     const bool xg_shape = b.k == 6 ? (b.tc_rows == 2 && !b.tc_splitk) : (b.k >= 4 && b.tc_rows == 1);
     // (6 targets with tc_gather = 4: the double-buffered exchange kernel)
+    // (4, 5 targets with tc_gather = 1: the exchange kernel staging two tiles
+    // ahead in shared memory by cp.async)
     const bool xg_pf = b.tc_prefetch == 1 || (b.k == 6 && b.tc_prefetch == 2);
-    b.tc_xg = b.tc && !tf32 && !b.tc_staged && xg_shape && xg_pf && opts.tc_exchange != 1 &&
+    b.tc_xg = b.tc && !tf32 && (!b.tc_staged || b.k <= 5) && xg_shape && xg_pf && opts.tc_exchange != 1 &&
               (opts.tc_exchange == 2 || tc_exchange_pays(b)) && tc_exchange_layout(n, b, xl);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }

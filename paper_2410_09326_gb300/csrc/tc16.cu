@@ -53,6 +53,10 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
 // One 16-byte core-matrix row of A from four scaled complex amplitudes
 // (re, im interleaved): hi = fp16(x), lo = fp16(x - hi).
 __device__ __forceinline__ void split_row(const float (&x)[8], uint4 &hi, uint4 &lo) {
@@ -440,12 +444,17 @@ template <int K> struct Tc16xOcc {
   static constexpr int value = K <= 4 ? 3 : 2;
 };
 
-template <int K>
-__global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
+// ST: the loads go to shared memory by cp.async, two tiles ahead (two
+// staging areas), instead of one tile ahead into registers; each thread
+// copies and later reads back exactly its own 16-byte chunks (consecutive
+// threads, consecutive chunks), so no barrier guards the staging areas.
+template <int K, bool ST>
+__global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value)
     k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                   int *__restrict__ err) {
   constexpr int D = 1 << K;
   constexpr int NV = D / 2;    // 16-byte registers per lane
+  constexpr uint32_t STAGE_BYTES = (uint32_t)NV * kTcThreads * 16u;
   constexpr int RB = K - 1;    // register bits
   constexpr int KR = 2 * D;
   constexpr uint32_t A_BYTES = 128u * KR * 2u;
@@ -459,6 +468,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
   unsigned char *sA_hi = smem;
   unsigned char *sA_lo = smem + A_BYTES;
   unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  unsigned char *sStage = sB + 2 * B_BYTES;  // ST: two staging areas
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
 
@@ -513,9 +523,44 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
     for (int r = 0; r < NV; r++)
       v[r] = valid ? *reinterpret_cast<const float4 *>(a + base + offset(r)) : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-  gather(tile);
+  // ST: tile t into staging area u (one commit group per tile, empty past the end)
+  uint64_t sbase0 = 0, sbase1 = 0;
+  bool svalid0 = false, svalid1 = false;
+  auto stage_in = [&](long long t, int u) {
+    const bool ok = t < p.n_tiles;
+    const uint64_t b = ok ? (insert_zeros((uint64_t)(t * 4 + warp), p.fixed, p.nf) | p.cmask) : 0;
+    if (u) {
+      sbase1 = b;
+      svalid1 = ok;
+    } else {
+      sbase0 = b;
+      svalid0 = ok;
+    }
+    if (ok) {
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int r = 0; r < NV; r++) cp_async16(dst + (uint32_t)r * kTcThreads * 16u, a + b + offset(r));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (ST) {
+    stage_in(tile, 0);
+    stage_in(tile + gridDim.x, 1);
+  } else {
+    gather(tile);
+  }
 
-  for (; tile < p.n_tiles; tile += gridDim.x) {
+  for (int it = 0; tile < p.n_tiles; tile += gridDim.x, it++) {
+    if constexpr (ST) {
+      // this tile's group has landed once at most the next one is pending
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const int u = it & 1;
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)r * kTcThreads * 16u);
+      base = u ? sbase1 : sbase0;
+      valid = u ? svalid1 : svalid0;
+    }
     xch.run<NV>(v);
     float mx = 0.f, nin = 0.f;
 #pragma unroll
@@ -557,7 +602,8 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
-    gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    if constexpr (ST) stage_in(tile + 2 * (long long)gridDim.x, it & 1);  // the area just read
+    else gather(tile + gridDim.x);  // next tile, in flight during the MMAs
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -602,6 +648,7 @@ __global__ void __launch_bounds__(kTcThreads, Tc16xOcc<K>::value)
       }
     }
   }
+  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
@@ -865,9 +912,6 @@ struct TcStageParam {
   unsigned short slot_lo[64], slot_hi[64];
 };
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
 
 template <int K>
 __global__ void __launch_bounds__(kTcThreads, 2)
@@ -1211,7 +1255,7 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool ST>
 cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
                       cudaStream_t s) {
   TcXParam p;
@@ -1226,23 +1270,27 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
   p.nswb = x.nswb;
   for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
   p.withhold_commit = b.withhold_commit ? 1 : 0;
-  const size_t smem = tc16_smem_bytes<K>();
+  // ST: two staging areas of one tile (2^(K-1) 16-byte chunks per thread)
+  const size_t smem = tc16_smem_bytes<K>() + (ST ? 2 * (size_t)(1 << (K - 1)) * kTcThreads * 16 : 0);
+  constexpr int want = ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value;
   static thread_local int configured = -1;
   static thread_local int per_sm = 1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc16x<K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16x<K>, kTcThreads, smem);
+    const int occ = resident_ctas((const void *)k_dense_tc16x<K, ST>, kTcThreads, smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
     const int tmem_cap = 512 / (4 << K);
-    per_sm = occ > Tc16xOcc<K>::value ? Tc16xOcc<K>::value : occ;
+    per_sm = occ > want ? want : occ;
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms * per_sm;
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16x<K><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16x<K, ST><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -1334,7 +1382,9 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
     if (b.k == 6) return b.tc_prefetch == 2 ? run_tc16x6<true>(a, n, b, x, dev_b, err, s)
                                             : run_tc16x6<false>(a, n, b, x, dev_b, err, s);
-    return b.k == 4 ? run_tc16x<4>(a, n, b, x, dev_b, err, s) : run_tc16x<5>(a, n, b, x, dev_b, err, s);
+    if (b.tc_staged)
+      return b.k == 4 ? run_tc16x<4, true>(a, n, b, x, dev_b, err, s) : run_tc16x<5, true>(a, n, b, x, dev_b, err, s);
+    return b.k == 4 ? run_tc16x<4, false>(a, n, b, x, dev_b, err, s) : run_tc16x<5, false>(a, n, b, x, dev_b, err, s);
   }
   if (b.tc_staged && (b.k == 4 || b.k == 5)) {
     static thread_local TcStageParam sp;  // large: kept off the stack; the launch copies it

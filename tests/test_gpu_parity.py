@@ -162,6 +162,47 @@ def test_tc_threads_per_group(n, k, rows, gather, split):
         assert np.linalg.norm(got - want) <= 1e-5
 
 
+@pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n", [12, 17, 20])
+def test_tc_lane_exchange_staged(n, k):
+    """4- and 5-target lane-exchange kernels with the loads staged two tiles
+    ahead in shared memory by cp.async (opts.tc_gather = 1): low and high
+    target patterns, a control, one tile (n = 12) to many, a partial last
+    wave, from a random state."""
+    rng = cg.SplitMix64(1900 + 10 * k + n)
+    o = qs.qs_default_opts()
+    o.tc_exchange = 2
+    o.tc_gather = 1
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    for pattern, ctrl in (([0, 1, 2, 3, 4], None), ([1, 2, 7, 9, 11], None), ([6, 7, 8, 9, 10], None),
+                          ([0, 3, 8, 9, 10], 6)):
+        qubits = pattern[:k]
+        if ctrl is None:
+            gates = []
+            for _ in range(2):
+                gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        else:
+            gates = []
+            for _ in range(2):
+                gates += [("cu3", [ctrl, q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("ccx", [ctrl, a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        width = k + (0 if ctrl is None else 1)
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(width) | qs.QS_TC, o)
+            _, recs = qs.qs_profile(st)
+            fits = n - k - (0 if ctrl is None else 1) >= 7
+            assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [2 if fits else 1]
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl)
+
+
 @pytest.mark.parametrize("n", [17, 19])
 def test_tc6_lane_exchange_double_buffered(n):
     """The 6-target lane-exchange kernel with two tiles in flight
@@ -478,13 +519,14 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
+@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 0, 1), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
 def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
     frees its TMEM and returns, and the next synchronising call reports
-    QS_ETIMEOUT. The state stays usable. Lane-exchange kernels (5 targets,
-    6 targets single- and double-buffered) and the thread-per-group ones."""
+    QS_ETIMEOUT. The state stays usable. Lane-exchange kernels (5 targets
+    with register or cp.async staging, 6 targets single- and double-buffered)
+    and the thread-per-group ones."""
     n = 14
     gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(k)] + [("cx", [q, q + 1]) for q in range(0, k - 1, 2)]
     gates += [("cx", [k - 2, k - 1])]
