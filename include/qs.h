@@ -117,9 +117,12 @@ typedef struct {
   int tile_k;           /* QS_TILE: fusion width inside a tile, 0 = 3; 1..4 */
   int tc_row_threads;   /* QS_TC with FP16 halves: threads sharing one group (row): 1, 2 or 4
                            (4 acts as 2 below 5 targets); 0 = 2 for 6-target blocks, else 1 */
-  int tc_gather;        /* QS_TC with FP16 halves: 0 = default (2); 1 = tiles staged through shared
-                           memory in address order (4, 5 targets); 2 = per-thread gathers, next
-                           tile gathered during the MMAs; 3 = per-thread gathers without that
+  int tc_gather;        /* QS_TC with FP16 halves: 0 = default: lane-exchange blocks of 4, 5
+                           targets stage their loads two tiles ahead in shared memory by
+                           cp.async, other blocks as 2; 1 = staged: the plain kernel copies
+                           tiles into shared memory in address order (4, 5 targets), exchange
+                           blocks as 0; 2 = per-thread gathers, next tile gathered into registers
+                           during the MMAs; 3 = per-thread gathers without that
                            prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
                            2 at 6); 4 = per-thread gathers two tiles ahead (same threads; for
                            6-target lane-exchange blocks: two tiles in flight through double-

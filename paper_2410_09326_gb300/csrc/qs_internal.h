@@ -64,7 +64,8 @@ struct Block {
   int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
   bool tc_splitk = false;         // 6-target tensor-core blocks: K in two halves (two CTAs per SM)
-  bool tc_xg = false;             // 4/5-target tensor-core blocks: lane-exchange gathers (tc16.cu)
+  bool tc_xg = false;             // 4..6-target tensor-core blocks: lane-exchange gathers (tc16.cu)
+  bool tc_xg_stage = false;       // exchange kernel (4, 5 targets): loads staged by cp.async, two tiles ahead
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,

@@ -1382,7 +1382,7 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
     if (b.k == 6) return b.tc_prefetch == 2 ? run_tc16x6<true>(a, n, b, x, dev_b, err, s)
                                             : run_tc16x6<false>(a, n, b, x, dev_b, err, s);
-    if (b.tc_staged)
+    if (b.tc_xg_stage)
       return b.k == 4 ? run_tc16x<4, true>(a, n, b, x, dev_b, err, s) : run_tc16x<5, true>(a, n, b, x, dev_b, err, s);
     return b.k == 4 ? run_tc16x<4, false>(a, n, b, x, dev_b, err, s) : run_tc16x<5, false>(a, n, b, x, dev_b, err, s);
   }

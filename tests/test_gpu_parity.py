@@ -232,11 +232,12 @@ def test_tc6_lane_exchange_double_buffered(n):
         assert np.linalg.norm(got - want) <= 1e-5, qubits
 
 
+@pytest.mark.parametrize("gather", [0, 2])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("ctrl", [None, 5, 0])
 @pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n", [12, 17])
-def test_tc_lane_exchange(n, k, ctrl, mode):
+def test_tc_lane_exchange(n, k, ctrl, mode, gather):
     """4-, 5- and 6-target (two threads per group, double-buffered)
     tensor-core blocks with lane-exchange gathers
     (opts.tc_exchange: 0 automatic, 1 never, 2 wherever the layout allows)
@@ -244,13 +245,15 @@ def test_tc_lane_exchange(n, k, ctrl, mode):
     or two lane/register exchanges, targets moved from lane to register bits
     to keep two), without a control,
     with a control on bit 5 and with bit 0 a control (no exchange layout),
-    one tile (n = 12) and many (n = 17), from a random state; the record's tc
+    one tile (n = 12) and many (n = 17), loads staged by cp.async (gather 0)
+    or gathered into registers (gather 2), from a random state; the record's tc
     field says which kernel ran (2 = lane exchange)."""
     if k == 6 and ctrl is not None:
         pytest.skip("a controlled 6-target block needs 7 fused qubits")
     rng = cg.SplitMix64(1300 + 10 * k + n + (ctrl or 0))
     o = qs.qs_default_opts()
     o.tc_exchange = mode
+    o.tc_gather = gather  # 0: 4/5-target exchange kernels stage by cp.async; 2: register gathers
     init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
     init /= np.linalg.norm(init)
     patterns = ([7, 8, 9, 10, 11], [1, 7, 8, 9, 10], [2, 7, 8, 9, 10], [3, 7, 8, 9, 10], [0, 7, 8, 9, 10],
@@ -519,7 +522,7 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 0, 1), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
+@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 0, 2), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
 def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
