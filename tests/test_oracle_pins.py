@@ -357,3 +357,31 @@ def test_mlp_linear_regime_closed_form():
     want = ((x @ w["W1"].T + w["b1"]) @ w["W2"].T + w["b2"]) @ w["w3"] + 0.5
     assert np.allclose(y, want, rtol=1e-13)
     assert mlp.N_PARAMS == 64 * 24 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def test_thread_count_applies_to_one_call_only():
+    """A thread count passed to one oracle call does not change the next
+    call's default (the OpenMP setting is restored), and the result does not
+    depend on the thread count."""
+    before = oracle.max_threads()
+    n, gates = cg.layered_swaps_circuit(3)
+    text = cg.to_qasm(n, gates)
+    one, perm1 = oracle.simulate(text, nthreads=1)
+    assert oracle.max_threads() == before
+    many, perm2 = oracle.simulate(text)
+    assert np.array_equal(perm1, perm2)
+    assert np.abs(one - many).max() < 1e-13
+
+
+def test_oracle_timing_helper_extrapolates_by_gate_count():
+    """The benchmark's oracle timing helper: a short circuit is timed whole,
+    a longer one on its first gates (at least three) and extrapolated by
+    gate count."""
+    import bench
+    n, gates = cg.layered_swaps_circuit(0)
+    text = cg.to_qasm(n, gates)
+    secs, timed, total, extrapolated = bench.time_oracle_sampled(text, 1, 1e-3)
+    assert total == len(gates) and 3 <= timed <= total and secs > 0
+    assert extrapolated == (timed < total)
+    secs, timed, total, extrapolated = bench.time_oracle_sampled(text, 1, 1e3)
+    assert timed == total and not extrapolated
