@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-// Lane-exchange variant (K = 4, 5; one thread per group; the next tile in
+// Lane-exchange variant (K = 4, 5; one thread per group; later tiles in
 // flight during the MMAs). Where targets sit among the lowest bits, the
 // thread-per-group gather above reads short runs per load instruction (16 or
 // 32 bytes when bit 1 or 2 is a target), so a warp touches many sectors per
@@ -444,10 +444,13 @@ template <int K> struct Tc16xOcc {
   static constexpr int value = K <= 4 ? 3 : 2;
 };
 
-// ST: the loads go to shared memory by cp.async, two tiles ahead (two
-// staging areas), instead of one tile ahead into registers; each thread
-// copies and later reads back exactly its own 16-byte chunks (consecutive
-// threads, consecutive chunks), so no barrier guards the staging areas.
+// ST (the default): the loads go to shared memory by cp.async, two tiles
+// ahead (two staging areas), instead of one tile ahead into registers; each
+// thread copies and later reads back exactly its own 16-byte chunks
+// (consecutive threads, consecutive chunks), so no barrier guards the staging
+// areas. Without registers held for tiles in flight the SM keeps four tiles
+// (128 KB at 5 targets) on the way instead of two: 5.95 -> 6.36 TB/s in the
+// n = 30 benchmark step on GB300.
 template <int K, bool ST>
 __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value)
     k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
