@@ -126,7 +126,8 @@ typedef struct {
                            prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
                            2 at 6); 4 = per-thread gathers two tiles ahead (same threads; for
                            6-target lane-exchange blocks: two tiles in flight through double-
-                           buffered operands and accumulators) */
+                           buffered operands and accumulators); 5 = per-thread gathers of 4, 5
+                           targets staged two tiles ahead in shared memory by cp.async */
   int fuse_lookahead;   /* fusion: where a gate could join several blocks or open a new one,
                            each choice is followed by this many gates of first-fit placement
                            and the one leaving the fewest blocks is taken; 0 = first fit

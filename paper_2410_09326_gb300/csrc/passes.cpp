@@ -682,8 +682,8 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     err = "opts.tc_exchange out of range (0..2)";
     return QS_EINVAL;
   }
-  if (opts.tc_gather < 0 || opts.tc_gather > 4) {
-    err = "opts.tc_gather out of range (0..4)";
+  if (opts.tc_gather < 0 || opts.tc_gather > 5) {
+    err = "opts.tc_gather out of range (0..5)";
     return QS_EINVAL;
   }
   if (opts.tc_row_threads < 0 || opts.tc_row_threads == 3 || opts.tc_row_threads > 4) {
@@ -859,6 +859,9 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     b.tc_splitk = b.tc && b.k == 6 && b.tc_rows == 2 && opts.tc_split_k == 1;
     b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
     b.tc_prefetch = opts.tc_gather == 3 ? 0 : (opts.tc_gather == 4 ? 2 : 1);
+    // per-thread gathers staged two tiles ahead by cp.async (4, 5 targets, one
+    // thread per group)
+    if (opts.tc_gather == 5 && b.tc_rows == 1 && (b.k == 4 || b.k == 5)) b.tc_prefetch = 3;
     // lane-exchange gathers where the plain gather reads short runs
     TcXLayout xl;
     const bool xg_shape = b.k == 6 ? (b.tc_rows == 2 && !b.tc_splitk) : (b.k >= 4 && b.tc_rows == 1);

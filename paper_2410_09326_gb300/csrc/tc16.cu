@@ -77,7 +77,7 @@ __device__ __forceinline__ void split_row(const float (&x)[8], uint4 &hi, uint4 
 // tile at the price of registers.
 template <int K, int TPR, int PFD = 1, bool SK = false> struct Tc16Occ {
   static constexpr int value =
-      SK ? 2 : TPR == 4 ? 1
+      SK ? 2 : PFD == 3 ? (K <= 4 ? 4 : 2) : TPR == 4 ? 1
                : (PFD == 1 ? (K <= 4 ? 4 : (K == 5 ? 3 : 1))
                            : (PFD == 0 ? (K <= 4 ? 6 : (K == 5 ? 4 : 1)) : (K <= 4 ? 3 : (K == 5 ? 2 : 1))));
 };
@@ -92,6 +92,11 @@ template <int K, int TPR, int PFD = 1, bool SK = false> struct Tc16Occ {
 // a time -- thread half h is exactly K half h -- so the MMAs run in two
 // rounds (half 0, wait, half 1) and the shared memory of 6-target blocks
 // drops from 128 KB to 96 KB: two CTAs fit per SM.
+// PFD = 3 (one thread per group, 4 or 5 targets): each thread copies its
+// group's amplitudes with cp.async two tiles ahead into one of two shared-
+// memory staging areas ([amplitude][thread], 8-byte elements, or 16-byte
+// pairs when bit 0 is a target) and reads them back at the top of the tile:
+// no registers hold tiles in flight.
 template <int K, int TPR, int PFD, bool SK = false>
 __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::value)
     k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
@@ -111,10 +116,14 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
   static_assert(DH % 4 == 0, "a thread converts whole 16-byte core-matrix rows");
   static_assert(!SK || TPR == 2, "split K pairs each thread half with a K half");
 
+  static_assert(PFD != 3 || (TPR == 1 && !SK), "staged copies: one thread per group");
+  constexpr uint32_t STAGE_BYTES = (uint32_t)DH * kTcThreads * 8u;
+
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *sA_hi = smem;
   unsigned char *sA_lo = smem + A_BYTES;
   unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  unsigned char *sStage = sB + 2 * B_BYTES;  // PFD = 3: two staging areas
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ float red_in[TPR > 1 ? 2 * NT : 1];   // (row max, row norm) partials of the inputs
@@ -181,11 +190,68 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
       for (int u = 0; u < DH; u++) v[u] = ok ? a[b + offset(s0 + u)] : make_float2(0.f, 0.f);
     }
   };
-  if (PFD >= 1) gather(tile, base, valid, v);
+  // PFD = 3: tile t into staging area u, one commit group per tile
+  uint64_t sbase0 = 0, sbase1 = 0;
+  bool svalid0 = false, svalid1 = false;
+  auto stage_in = [&](long long t, int u) {
+    const long long g = t * kTcThreads + r;
+    const bool ok = t < p.n_tiles && g < p.n_groups;
+    const uint64_t b = ok ? (insert_zeros((uint64_t)g, p.fixed, p.nf) | p.cmask) : 0;
+    if (u) {
+      sbase1 = b;
+      svalid1 = ok;
+    } else {
+      sbase0 = b;
+      svalid0 = ok;
+    }
+    if (ok) {
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES;
+      if (pair) {
+#pragma unroll
+        for (int w = 0; w < DH / 2; w++)
+          cp_async16(dst + ((uint32_t)w * kTcThreads + (uint32_t)tid) * 16u, a + b + offset(2 * w));
+      } else {
+#pragma unroll
+        for (int w = 0; w < DH; w++)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst + ((uint32_t)w * kTcThreads +
+                                                                                  (uint32_t)tid) * 8u),
+                       "l"(a + b + offset(w))
+                       : "memory");
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (PFD == 3) {
+    stage_in(tile, 0);
+    stage_in(tile + gridDim.x, 1);
+  }
+  if (PFD == 1 || PFD == 2) gather(tile, base, valid, v);
   if (PFD == 2) gather(tile + gridDim.x, base2, valid2, v2);
 
-  for (; tile < p.n_tiles; tile += gridDim.x) {
+  for (int it = 0; tile < p.n_tiles; tile += gridDim.x, it++) {
     if (PFD == 0) gather(tile, base, valid, v);
+    if constexpr (PFD == 3) {
+      // this tile's group has landed once at most the next one is pending
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const int u = it & 1;
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
+      base = u ? sbase1 : sbase0;
+      valid = u ? svalid1 : svalid0;
+      if (pair) {
+#pragma unroll
+        for (int w = 0; w < DH / 2; w++) {
+          const float4 x = valid ? *reinterpret_cast<const float4 *>(src + ((uint32_t)w * kTcThreads + tid) * 16u)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[2 * w] = make_float2(x.x, x.y);
+          v[2 * w + 1] = make_float2(x.z, x.w);
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < DH; w++)
+          v[w] = valid ? *reinterpret_cast<const float2 *>(src + ((uint32_t)w * kTcThreads + tid) * 8u)
+                       : make_float2(0.f, 0.f);
+      }
+    }
     // row scale: largest component into [0.5, 1)
     float mx = 0.f, nin = 0.f;
 #pragma unroll
@@ -274,6 +340,7 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
+    if (PFD == 3) stage_in(tile + 2 * (long long)gridDim.x, it & 1);  // the area just read
     if (PFD == 1) gather(tile + gridDim.x, base, valid, v);  // next tile, in flight during the MMAs
     if (PFD == 2) {
       // the tile after next goes in flight; the next one (loaded during the
@@ -344,6 +411,7 @@ __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::va
       }
     }
   }
+  if constexpr (PFD == 3) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
@@ -1234,7 +1302,8 @@ cudaError_t run_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *e
   p.withhold_commit = b.withhold_commit ? 1 : 0;
   fill_fixed(b, p.fixed, p.nf);
   for (int j = 0; j < K; j++) p.tq[j] = b.q[j];
-  const size_t smem = SK ? tc16_smem_bytes<K>() - (size_t)128 * (2 << K) * 2 : tc16_smem_bytes<K>();
+  const size_t smem = SK ? tc16_smem_bytes<K>() - (size_t)128 * (2 << K) * 2
+                          : tc16_smem_bytes<K>() + (PFD == 3 ? 2 * (size_t)(1 << K) * kTcThreads * 8 : 0);
   // per device: opt in to the shared memory and size one wave of resident
   // CTAs; TMEM columns stay within 512 per SM (4 x 64, 3 x 128, 1 x 256)
   static thread_local int configured = -1;
@@ -1392,6 +1461,10 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
   if (b.tc_staged && (b.k == 4 || b.k == 5)) {
     static thread_local TcStageParam sp;  // large: kept off the stack; the launch copies it
     if (stage_param(n, b, sp)) return b.k == 4 ? run_tc16s<4>(a, sp, dev_b, err, s) : run_tc16s<5>(a, sp, dev_b, err, s);
+  }
+  if (b.tc_prefetch == 3 && b.tc_rows == 1) {
+    if (b.k == 4) return run_tc16<4, 1, 3>(a, n, b, dev_b, err, s);
+    if (b.k == 5) return run_tc16<5, 1, 3>(a, n, b, dev_b, err, s);
   }
   if (b.tc_prefetch == 0 && b.tc_rows == 1) {
     if (b.k == 4) return run_tc16<4, 1, 0>(a, n, b, dev_b, err, s);

@@ -163,6 +163,44 @@ def test_tc_threads_per_group(n, k, rows, gather, split):
 
 
 @pytest.mark.parametrize("k", [4, 5])
+@pytest.mark.parametrize("n", [10, 13, 18])
+def test_tc_plain_gather_staged(n, k):
+    """The thread-per-group tensor-core kernel (no lane exchange) with its
+    per-thread gathers staged two tiles ahead by cp.async (opts.tc_gather =
+    5): 8-byte copies, 16-byte pairs when bit 0 is a target, a control, a
+    partial tile (n = 10) and many tiles, from a random state."""
+    rng = cg.SplitMix64(2100 + 10 * k + n)
+    o = qs.qs_default_opts()
+    o.tc_exchange = 1
+    o.tc_gather = 5
+    init = np.array([rng.uniform(-1, 1) + 1j * rng.uniform(-1, 1) for _ in range(1 << n)])
+    init /= np.linalg.norm(init)
+    for pattern, ctrl in (([0, 1, 2, 3, 4], None), ([1, 2, 5, 7, 9], None), ([n - 5, n - 4, n - 3, n - 2, n - 1], None),
+                          ([0, 3, 5, 7, 8], 9)):
+        qubits = pattern[:k]
+        gates = []
+        for _ in range(2):
+            if ctrl is None:
+                gates += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("cx", [a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+            else:
+                gates += [("cu3", [ctrl, q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in qubits]
+                gates += [("ccx", [ctrl, a, b]) for a, b in zip(qubits[:-1], qubits[1:])]
+        width = k + (0 if ctrl is None else 1)
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        st = qs.qs_alloc_state(n, qs.QS_C64)
+        try:
+            qs.qs_write_state(st, init.astype(np.complex64))
+            qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_FUSE | qs.QS_FUSE_K(width) | qs.QS_TC, o)
+            _, recs = qs.qs_profile(st)
+            assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [1]
+            got = qs.qs_read_state(st, n, qs.QS_C64).astype(np.complex128)
+        finally:
+            qs.qs_free_state(st)
+        assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl)
+
+
+@pytest.mark.parametrize("k", [4, 5])
 @pytest.mark.parametrize("n", [12, 17, 20])
 def test_tc_lane_exchange_staged(n, k):
     """4- and 5-target lane-exchange kernels with the loads staged two tiles
@@ -529,7 +567,8 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 0, 2), (5, 1, 0), (6, 2, 0), (6, 2, 4), (6, 1, 0)])
+@pytest.mark.parametrize("k,exchange,gather", [(5, 0, 0), (5, 0, 2), (5, 1, 0), (5, 1, 5), (6, 2, 0), (6, 2, 4),
+                                                (6, 1, 0)])
 def test_bounded_wait_times_out_and_state_recovers(k, exchange, gather):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
