@@ -92,11 +92,14 @@ template <int K, int TPR, int PFD = 1, bool SK = false> struct Tc16Occ {
 // a time -- thread half h is exactly K half h -- so the MMAs run in two
 // rounds (half 0, wait, half 1) and the shared memory of 6-target blocks
 // drops from 128 KB to 96 KB: two CTAs fit per SM.
-// PFD = 3 (one thread per group, 4 or 5 targets): each thread copies its
-// group's amplitudes with cp.async two tiles ahead into one of two shared-
-// memory staging areas ([amplitude][thread], 8-byte elements, or 16-byte
-// pairs when bit 0 is a target) and reads them back at the top of the tile:
-// no registers hold tiles in flight.
+// PFD = 3 (one thread per group, 4 or 5 targets; opt-in): each thread copies
+// its group's amplitudes with cp.async two tiles ahead into one of two
+// shared-memory staging areas ([amplitude][thread], 8-byte elements, or
+// 16-byte pairs when bit 0 is a target) and reads them back at the top of the
+// tile: no registers hold tiles in flight. Measured on GB300 the 8-byte
+// copies cost more than they hide (4.6-5.9 vs 5.6-6.3 TB/s), except for
+// 16-byte pairs at 5 targets; the exchange kernel's 16-byte staging is the
+// default instead.
 template <int K, int TPR, int PFD, bool SK = false>
 __global__ void __launch_bounds__(kTcThreads * TPR, Tc16Occ<K, TPR, PFD, SK>::value)
     k_dense_tc16(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcParam p,
