@@ -875,7 +875,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     // memory unless per-thread register gathers are asked for: measured on
     // GB300 from random states at n = 28, 5 targets 5102-6302 GB/s staged vs
     // 5177-5978 in registers, 4 targets with low targets 5753-6100 vs 5259-5521
-    b.tc_xg_stage = b.tc_xg && b.k <= 5 && opts.tc_gather != 2;
+    b.tc_xg_stage = b.tc_xg && opts.tc_gather != 2 && (b.k <= 5 || b.tc_prefetch == 1);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;

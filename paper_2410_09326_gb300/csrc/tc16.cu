@@ -634,6 +634,9 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
       for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)r * kTcThreads * 16u);
       base = u ? sbase1 : sbase0;
       valid = u ? svalid1 : svalid0;
+      // the area is free again (this thread's own chunks): refill it at once,
+      // so two tiles stay in flight through the whole tile
+      stage_in(tile + 2 * (long long)gridDim.x, u);
     }
     xch.run<NV>(v);
     float mx = 0.f, nin = 0.f;
@@ -676,8 +679,7 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
-    if constexpr (ST) stage_in(tile + 2 * (long long)gridDim.x, it & 1);  // the area just read
-    else gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    if constexpr (!ST) gather(tile + gridDim.x);  // next tile, in flight during the MMAs
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -745,7 +747,12 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
 // vs 4.40-5.51 TB/s): the next tile's loads then have only the stores to
 // arrive in, instead of the MMAs and the stores, and one CTA cannot hide the
 // rest of their latency. DB = false keeps the order of the other kernels.
-template <bool DB>
+// ST (single buffer, the default): the loads go to a 64 KB shared-memory
+// staging area by cp.async; a thread refills its own chunks right after
+// reading them back at the top of a tile, so the next tile is in flight
+// through the whole tile (register gathers can only be issued once the
+// convert has freed the registers).
+template <bool DB, bool ST>
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
@@ -761,8 +768,12 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after the buffers
+  static_assert(!(DB && ST), "staging keeps one A buffer");
+  constexpr uint32_t STAGE_BYTES = (uint32_t)NV * NT * 16u;
+  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after the
+  // buffers; ST: the staging area after B
   unsigned char *sB = smem + (DB ? 4 : 2) * A_BYTES;
+  unsigned char *sStage = sB + 2 * B_BYTES;
   __shared__ __align__(8) uint64_t mbar[3];  // per buffer; [2] for the final drain
   __shared__ uint32_t tmem_slot;
   __shared__ float red_in[2 * NT];
@@ -872,13 +883,34 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   float prev_nin = 0.f;
   int it = 0;
   long long tile = blockIdx.x;
-  gather(tile);
+  // ST: tile t into the staging area (one commit group, empty past the end)
+  uint64_t sbase = 0;
+  auto stage_in = [&](long long t) {
+    const bool ok = t < p.n_tiles;
+    sbase = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
+    if (ok) {
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + sbase + offset(q));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (ST) stage_in(tile);
+  else gather(tile);
   for (;; tile += gridDim.x, it++) {
     const bool have = tile < p.n_tiles;
     const int buf = DB ? (it & 1) : 0;
     uint64_t cur_base = 0;
     float cur_nin = 0.f;
     if (have) {
+      if constexpr (ST) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const unsigned char *src = sStage + (uint32_t)tid * 16u;
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
+        base = sbase;
+        stage_in(tile + gridDim.x);  // own chunks only: refill at once
+      }
       xch.run<NV>(v);
       float mx = 0.f, nin = 0.f;
 #pragma unroll
@@ -928,7 +960,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       }
       cur_base = base;
       cur_nin = nin;
-      gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
+      if constexpr (!ST) gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
     }
     if (DB && prev) {
       // the previous tile (other buffer) while this one's MMAs run
@@ -949,6 +981,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     prev_base = cur_base;
     prev_nin = cur_nin;
   }
+  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
@@ -1369,7 +1402,7 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
   return cudaGetLastError();
 }
 
-template <bool DB>
+template <bool DB, bool ST>
 cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
                        cudaStream_t s) {
   TcXParam p;
@@ -1385,20 +1418,24 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
   for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
   p.th = x.th;
   p.withhold_commit = b.withhold_commit ? 1 : 0;
-  // one or two A buffers (hi + lo) of 64 KB and B (hi + lo) of 64 KB
-  const size_t smem = (DB ? 4 : 2) * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
+  // one or two A buffers (hi + lo) of 64 KB, B (hi + lo) of 64 KB, ST: a
+  // 64 KB staging area
+  const size_t smem = (DB ? 4 : 2) * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2 +
+                      (ST ? (size_t)16 * 2 * kTcThreads * 16 : 0);
   static thread_local int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6<DB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc16x6<DB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (resident_ctas((const void *)k_dense_tc16x6<DB>, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    if (resident_ctas((const void *)k_dense_tc16x6<DB, ST>, 2 * kTcThreads, smem) < 1)
+      return cudaErrorInvalidConfiguration;
     configured = dev;
   }
   long long grid = (long long)dev_info().sms;  // one CTA per SM (512 TMEM columns each)
   if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16x6<DB><<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16x6<DB, ST><<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -1455,8 +1492,11 @@ cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, 
     // B was built in slot order: no other kernel can take this block
     TcXLayout x;
     if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
-    if (b.k == 6) return b.tc_prefetch == 2 ? run_tc16x6<true>(a, n, b, x, dev_b, err, s)
-                                            : run_tc16x6<false>(a, n, b, x, dev_b, err, s);
+    if (b.k == 6) {
+      if (b.tc_prefetch == 2) return run_tc16x6<true, false>(a, n, b, x, dev_b, err, s);
+      return b.tc_xg_stage ? run_tc16x6<false, true>(a, n, b, x, dev_b, err, s)
+                           : run_tc16x6<false, false>(a, n, b, x, dev_b, err, s);
+    }
     if (b.tc_xg_stage)
       return b.k == 4 ? run_tc16x<4, true>(a, n, b, x, dev_b, err, s) : run_tc16x<5, true>(a, n, b, x, dev_b, err, s);
     return b.k == 4 ? run_tc16x<4, false>(a, n, b, x, dev_b, err, s) : run_tc16x<5, false>(a, n, b, x, dev_b, err, s);
