@@ -866,16 +866,15 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     TcXLayout xl;
     const bool xg_shape = b.k == 6 ? (b.tc_rows == 2 && !b.tc_splitk) : (b.k >= 4 && b.tc_rows == 1);
     // (6 targets with tc_gather = 4: the double-buffered exchange kernel)
-    // (4, 5 targets with tc_gather = 1: the exchange kernel staging two tiles
-    // ahead in shared memory by cp.async)
     const bool xg_pf = b.tc_prefetch == 1 || (b.k == 6 && b.tc_prefetch == 2);
-    b.tc_xg = b.tc && !tf32 && (!b.tc_staged || b.k <= 5) && xg_shape && xg_pf && opts.tc_exchange != 1 &&
+    b.tc_xg = b.tc && !tf32 && xg_shape && xg_pf && opts.tc_exchange != 1 &&
               (opts.tc_exchange == 2 || tc_exchange_pays(b)) && tc_exchange_layout(n, b, xl);
     // the 4/5-target exchange kernel stages its loads two tiles ahead in shared
     // memory unless per-thread register gathers are asked for: measured on
     // GB300 from random states at n = 28, 5 targets 5102-6302 GB/s staged vs
     // 5177-5978 in registers, 4 targets with low targets 5753-6100 vs 5259-5521
-    b.tc_xg_stage = b.tc_xg && opts.tc_gather != 2 && (b.k <= 5 || b.tc_prefetch == 1);
+    // (6 targets: staged only when asked for with tc_gather = 1, measured slower)
+    b.tc_xg_stage = b.tc_xg && (b.k <= 5 ? opts.tc_gather != 2 : opts.tc_gather == 1 && b.tc_prefetch == 1);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
   }
   return QS_OK;

@@ -634,9 +634,6 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
       for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)r * kTcThreads * 16u);
       base = u ? sbase1 : sbase0;
       valid = u ? svalid1 : svalid0;
-      // the area is free again (this thread's own chunks): refill it at once,
-      // so two tiles stay in flight through the whole tile
-      stage_in(tile + 2 * (long long)gridDim.x, u);
     }
     xch.run<NV>(v);
     float mx = 0.f, nin = 0.f;
@@ -679,7 +676,10 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
-    if constexpr (!ST) gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    // ST: refill the area just read (this thread's own chunks). Refilling it
+    // right after the read instead measured 0.5-1.8% slower on GB300.
+    if constexpr (ST) stage_in(tile + 2 * (long long)gridDim.x, it & 1);
+    else gather(tile + gridDim.x);  // next tile, in flight during the MMAs
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -747,11 +747,14 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
 // vs 4.40-5.51 TB/s): the next tile's loads then have only the stores to
 // arrive in, instead of the MMAs and the stores, and one CTA cannot hide the
 // rest of their latency. DB = false keeps the order of the other kernels.
-// ST (single buffer, the default): the loads go to a 64 KB shared-memory
-// staging area by cp.async; a thread refills its own chunks right after
-// reading them back at the top of a tile, so the next tile is in flight
-// through the whole tile (register gathers can only be issued once the
-// convert has freed the registers).
+// ST (single buffer; opt-in, opts.tc_gather = 1): the loads go to a 64 KB
+// shared-memory staging area by cp.async; a thread refills its own chunks
+// right after reading them back at the top of a tile, so the next tile is in
+// flight through the whole tile (register gathers can only be issued once
+// the convert has freed the registers). Measured on GB300 it is 4-8% slower
+// than the register gathers (4.08-5.19 vs 4.41-5.51 TB/s): with one CTA per
+// SM the copies' issue and the shared-memory round trip cost more than the
+// longer flight gains.
 template <bool DB, bool ST>
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
