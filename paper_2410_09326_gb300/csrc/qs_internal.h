@@ -64,7 +64,7 @@ struct Block {
   int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
   bool tc_splitk = false;         // 6-target tensor-core blocks: K in two halves (two CTAs per SM)
-  bool tc_xg = false;             // 4..6-target tensor-core blocks: lane-exchange gathers (tc16.cu)
+  bool tc_xg = false;             // 4..6-target tensor-core blocks: lane-exchange gathers (tc16x.cu)
   bool tc_xg_stage = false;       // exchange kernel (4, 5 targets): loads staged by cp.async, two tiles ahead
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
@@ -81,7 +81,7 @@ struct Block {
 };
 
 // Lane-exchange layout of a 4-, 5- or 6-target FP16 tensor-core block
-// (tc16.cu; 6 targets: two threads per group, each half laid out as a
+// (tc16x.cu; 6 targets: two threads per group, each half laid out as a
 // 5-target block with the highest target fixed).
 // A warp owns the sub-cube of 32 groups spanned by the targets and the five
 // lowest free bits. It loads it in address order -- element bit of each

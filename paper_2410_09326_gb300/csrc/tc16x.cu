@@ -1,0 +1,801 @@
+// Dense fused blocks of 4..6 targets on the tensor cores (FP16 operand
+// halves, as in tc16.cu) with lane-exchange gathers: a warp loads the
+// sub-cube spanned by a block's targets and its five lowest free bits in
+// address order and exchanges bits between lanes, registers and the 16-byte
+// element with warp shuffles until each lane holds one whole group; B is built
+// in the same "slot" order (tc16_build_b). The host layout (which bits sit on
+// lanes and registers, which exchanges run) is tc_exchange_layout below; the
+// planner picks these kernels where tc_exchange_pays.
+#include <cstdint>
+#include <cstring>
+#include <type_traits>
+
+#include "tc16_common.cuh"
+
+namespace qs {
+namespace kern {
+
+namespace {
+
+// Lane-exchange variant (K = 4, 5; one thread per group; later tiles in
+// flight during the MMAs). Where targets sit among the lowest bits, the
+// thread-per-group gather above reads short runs per load instruction (16 or
+// 32 bytes when bit 1 or 2 is a target), so a warp touches many sectors per
+// instruction. Here warp w of a tile owns the sub-cube of its 32 groups
+// (targets + the five lowest free bits; the other bits fixed per warp item)
+// and loads it in address order: 16-byte loads whose element bit is bit 0,
+// lanes over the next five bits, registers over the rest. Warp shuffles then
+// exchange position bits -- the element bit with a lane bit (half of every
+// register moves), lane bits with register bits (half of the registers
+// move) -- until each lane holds one whole group, its amplitudes in slot
+// order (slot bit 0 = element bit, 1 + j = register bit j). B is built on the
+// host with its rows and columns in the same slot order, so the product comes
+// out in slot order, the same exchanges (involutions on disjoint bit pairs)
+// restore the load layout 8 slots at a time, and the warp stores as it loaded.
+struct TcXParam {
+  long long n_tiles;          // tiles of 128 groups = 4 warp items of 32
+  unsigned long long cmask;
+  int nf;                     // fixed bits of the warp item index
+  int fixed[kMaxFixed];
+  int lbit[5];                // physical bit of lane bit i (load layout)
+  int rbit[5];                // physical bit of register bit j (load layout)
+  int la;                     // lane bit exchanged with the element bit, -1: none
+  int nswb;                   // lane bits lb[i] exchanged with register bits i
+  int lb[2];
+  int th;                     // 6 targets: the target bit thread half h fixes (the highest)
+  int withhold_commit;
+};
+
+// The exchanges of the lane-exchange kernels, on N consecutive 16-byte
+// registers starting at a multiple of 4 (register bits 0 and 1 of the pairs
+// lie inside any such run): first the element bit with lane bit la -- half
+// of every register crosses: lane bit 0 keeps the element-0 half and trades
+// its element-1 half for the partner's element-0 half, lane bit 1 the other
+// way round -- then lane bit lb[i] with register bit i (half of the
+// registers cross). Each is an involution on its own pair of bits and the
+// pairs are disjoint, so running them again restores the load layout.
+struct LaneExchange {
+  int la, nswb, lb0, lb1, lane;
+  __device__ __forceinline__ LaneExchange(const TcXParam &p, int lane_)
+      : la(p.la), nswb(p.nswb), lb0(p.lb[0]), lb1(p.lb[1]), lane(lane_) {}
+  template <int N> __device__ __forceinline__ void run(float4 *w) const {
+    if (la >= 0) {
+      const bool up = (lane >> la) & 1;
+      const unsigned m = 1u << la;
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        const float s0 = up ? w[q].x : w[q].z, s1 = up ? w[q].y : w[q].w;
+        const float r0 = __shfl_xor_sync(0xffffffffu, s0, m), r1 = __shfl_xor_sync(0xffffffffu, s1, m);
+        if (up) {
+          w[q].x = r0;
+          w[q].y = r1;
+        } else {
+          w[q].z = r0;
+          w[q].w = r1;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      if (i >= nswb) break;
+      const int lbi = i == 0 ? lb0 : lb1;
+      const bool up = (lane >> lbi) & 1;
+#pragma unroll
+      for (int q = 0; q < N; q++) {
+        if ((q >> i) & 1) continue;
+        const int q2 = q | (1 << i);
+        const float4 snd = up ? w[q] : w[q2];
+        float4 rcv;
+        rcv.x = __shfl_xor_sync(0xffffffffu, snd.x, 1u << lbi);
+        rcv.y = __shfl_xor_sync(0xffffffffu, snd.y, 1u << lbi);
+        rcv.z = __shfl_xor_sync(0xffffffffu, snd.z, 1u << lbi);
+        rcv.w = __shfl_xor_sync(0xffffffffu, snd.w, 1u << lbi);
+        if (up) w[q] = rcv;
+        else w[q2] = rcv;
+      }
+    }
+  }
+};
+
+// Resident CTAs per SM of the exchange kernel (registers per thread follow).
+// Measured on GB300 from random states at n = 28: spill-free registers beat
+// more resident CTAs -- 5 targets at 2 CTAs (237 registers) ran 5413-6024
+// GB/s, at 3 (168, spilling) 5386-5913, at 4 (128) 4053-4119; 4 targets at
+// 3 CTAs (153 registers) 5508-5858, at 4 (128, spilling) 5344-5728.
+template <int K> struct Tc16xOcc {
+  static constexpr int value = K <= 4 ? 3 : 2;
+};
+
+// ST (the default): the loads go to shared memory by cp.async, two tiles
+// ahead (two staging areas), instead of one tile ahead into registers; each
+// thread copies and later reads back exactly its own 16-byte chunks
+// (consecutive threads, consecutive chunks), so no barrier guards the staging
+// areas. Without registers held for tiles in flight the SM keeps four tiles
+// (128 KB at 5 targets) on the way instead of two: 5.95 -> 6.36 TB/s in the
+// n = 30 benchmark step on GB300.
+template <int K, bool ST>
+__global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value)
+    k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
+                  int *__restrict__ err) {
+  constexpr int D = 1 << K;
+  constexpr int NV = D / 2;    // 16-byte registers per lane
+  constexpr uint32_t STAGE_BYTES = (uint32_t)NV * kTcThreads * 16u;
+  constexpr int RB = K - 1;    // register bits
+  constexpr int KR = 2 * D;
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t NCOLS = 2 * KR;
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA_hi = smem;
+  unsigned char *sA_lo = smem + A_BYTES;
+  unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  unsigned char *sStage = sB + 2 * B_BYTES;  // ST: two staging areas
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += kTcThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t mbar_a = smem_addr(&mbar);
+  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+  const uint32_t row_off = (uint32_t)(tid >> 3) * SBO + (uint32_t)(tid & 7) * 16u;
+
+  uint64_t lane_off = 0;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
+  uint64_t roff[RB];
+#pragma unroll
+  for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
+  auto offset = [&](int rr) {
+    uint64_t o = lane_off;
+#pragma unroll
+    for (int j = 0; j < RB; j++)
+      if ((rr >> j) & 1) o += roff[j];
+    return o;
+  };
+  const LaneExchange xch(p, lane);
+
+  uint32_t phase = 0;
+  bool aborted = false;
+  long long tile = blockIdx.x;
+  float4 v[NV];
+  uint64_t base = 0;
+  bool valid = false;
+  auto gather = [&](long long t) {
+    valid = t < p.n_tiles;  // uniform over the CTA
+    base = valid ? (insert_zeros((uint64_t)(t * 4 + warp), p.fixed, p.nf) | p.cmask) : 0;
+#pragma unroll
+    for (int r = 0; r < NV; r++)
+      v[r] = valid ? *reinterpret_cast<const float4 *>(a + base + offset(r)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  // ST: tile t into staging area u (one commit group per tile, empty past the end)
+  uint64_t sbase0 = 0, sbase1 = 0;
+  bool svalid0 = false, svalid1 = false;
+  auto stage_in = [&](long long t, int u) {
+    const bool ok = t < p.n_tiles;
+    const uint64_t b = ok ? (insert_zeros((uint64_t)(t * 4 + warp), p.fixed, p.nf) | p.cmask) : 0;
+    if (u) {
+      sbase1 = b;
+      svalid1 = ok;
+    } else {
+      sbase0 = b;
+      svalid0 = ok;
+    }
+    if (ok) {
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int r = 0; r < NV; r++) cp_async16(dst + (uint32_t)r * kTcThreads * 16u, a + b + offset(r));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (ST) {
+    stage_in(tile, 0);
+    stage_in(tile + gridDim.x, 1);
+  } else {
+    gather(tile);
+  }
+
+  for (int it = 0; tile < p.n_tiles; tile += gridDim.x, it++) {
+    if constexpr (ST) {
+      // this tile's group has landed once at most the next one is pending
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      const int u = it & 1;
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)r * kTcThreads * 16u);
+      base = u ? sbase1 : sbase0;
+      valid = u ? svalid1 : svalid0;
+    }
+    xch.run<NV>(v);
+    float mx = 0.f, nin = 0.f;
+#pragma unroll
+    for (int r = 0; r < NV; r++) {
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[r].x), fabsf(v[r].y)), fmaxf(fabsf(v[r].z), fabsf(v[r].w))));
+      nin = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, fmaf(v[r].z, v[r].z, fmaf(v[r].w, v[r].w, nin))));
+    }
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+    // slots 4c..4c+3 (registers 2c, 2c + 1) fill the 16-byte row of core matrix c
+#pragma unroll
+    for (int c = 0; c < D / 4; c++) {
+      const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
+                          v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
+      uint4 hi, lo;
+      split_row(x, hi, lo);
+      *reinterpret_cast<uint4 *>(sA_hi + row_off + c * LBO) = hi;
+      *reinterpret_cast<uint4 *>(sA_lo + row_off + c * LBO) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ks++) {
+        const uint32_t koff = (uint32_t)ks * 2u * LBO;
+        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        mma_f16(tmem, dah, dbh, IDESC, acc);
+        mma_f16(tmem + KR, dah, dbl, IDESC, acc);
+        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+      }
+      if (!p.withhold_commit) mma_commit(mbar_a);
+    }
+    const uint64_t cur_base = base;
+    const bool cur_valid = valid;
+    // ST: refill the area just read (this thread's own chunks). Refilling it
+    // right after the read instead measured 0.5-1.8% slower on GB300.
+    if constexpr (ST) stage_in(tile + 2 * (long long)gridDim.x, it & 1);
+    else gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    const bool ok = mbar_wait(mbar_a, phase);
+    phase ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      aborted = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    float nout = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < KR / 16; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+    // 8 slots (4 registers) at a time: scale, exchange back, store
+#pragma unroll
+    for (int hh = 0; hh < KR / 16; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(lane_base + 16 * hh, rb);
+      TmemLd<16>::run(lane_base + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float4 y[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
+                           (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
+                           (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
+                           (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
+      xch.run<4>(y);
+      if (cur_valid) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
+      }
+    }
+  }
+  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) {
+    if (tid == 0) mma_commit(mbar_a);
+    mbar_wait(mbar_a, phase ^ 1);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+// Six targets: the same lane exchange with two threads per group. Thread
+// (h, r), h = tid / 128, holds the 32 amplitudes of group r whose highest
+// target equals h: warp w and warp w + 4 load the same 32 groups' two halves,
+// each exactly as a 5-target exchange warp (the highest target fixed per
+// half; slot bit 5 = the highest target). The row's scale and norms are
+// combined over the two halves through shared memory. The 6-target operands
+// fill an SM with one CTA, which idles while its MMAs run (about a fifth of
+// a tile); DB = true double-buffers the A operands (64 KB per tile) and the
+// TMEM accumulators (256 columns per tile) so that the MMAs of tile i run
+// while the CTA stores tile i - 1. Measured on GB300 that is slower (4.08-4.63
+// vs 4.40-5.51 TB/s): the next tile's loads then have only the stores to
+// arrive in, instead of the MMAs and the stores, and one CTA cannot hide the
+// rest of their latency. DB = false keeps the order of the other kernels.
+// ST (single buffer; opt-in, opts.tc_gather = 1): the loads go to a 64 KB
+// shared-memory staging area by cp.async; a thread refills its own chunks
+// right after reading them back at the top of a tile, so the next tile is in
+// flight through the whole tile (register gathers can only be issued once
+// the convert has freed the registers). Measured on GB300 it is 4-8% slower
+// than the register gathers (4.08-5.19 vs 4.41-5.51 TB/s): with one CTA per
+// SM the copies' issue and the shared-memory round trip cost more than the
+// longer flight gains.
+template <bool DB, bool ST>
+__global__ void __launch_bounds__(2 * kTcThreads, 1)
+    k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
+                   int *__restrict__ err) {
+  constexpr int NT = 2 * kTcThreads;
+  constexpr int NV = 16;        // 16-byte registers per thread (32 amplitudes)
+  constexpr int RB = 4;         // register bits
+  constexpr int KR = 128;       // real K = N
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;     // one of hi / lo, one tile
+  constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t SBO = (KR / 8) * 128u;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t NCOLS = 512;                  // two tiles x (large + small)
+  constexpr uint32_t IDESC = make_idesc_f16(128, KR);
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  static_assert(!(DB && ST), "staging keeps one A buffer");
+  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after the
+  // buffers; ST: the staging area after B
+  unsigned char *sB = smem + (DB ? 4 : 2) * A_BYTES;
+  unsigned char *sStage = sB + 2 * B_BYTES;
+  __shared__ __align__(8) uint64_t mbar[3];  // per buffer; [2] for the final drain
+  __shared__ uint32_t tmem_slot;
+  __shared__ float red_in[2 * NT];
+  __shared__ float red_out[NT];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int r = tid & 127;
+  const int h = tid >> 7;
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += NT) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(NCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int u = 0; u < 3; u++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[u])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+
+  uint64_t lane_off = h ? (1ull << p.th) : 0ull;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+    if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
+  uint64_t roff[RB];
+#pragma unroll
+  for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
+  auto offset = [&](int rr) {
+    uint64_t o = lane_off;
+#pragma unroll
+    for (int j = 0; j < RB; j++)
+      if ((rr >> j) & 1) o += roff[j];
+    return o;
+  };
+  const LaneExchange xch(p, lane);
+
+  float4 v[NV];
+  uint64_t base = 0;
+  auto gather = [&](long long t) {
+    const bool ok = t < p.n_tiles;  // uniform over the CTA
+    base = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
+#pragma unroll
+    for (int q = 0; q < NV; q++)
+      v[q] = ok ? *reinterpret_cast<const float4 *>(a + base + offset(q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+
+  uint32_t ph0 = 0, ph1 = 0;   // parity each buffer's barrier waits for next
+  // wait for the MMAs of the tile in buffer pb, store it; false: timed out
+  auto epilogue = [&](int pb, uint64_t pbase, float pnin) -> bool {
+    const bool ok = mbar_wait(smem_addr(&mbar[pb]), pb ? ph1 : ph0);
+    if (pb) ph1 ^= 1;
+    else ph0 ^= 1;
+    if (!__syncthreads_and(ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      return false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t cb = lane_base + (uint32_t)pb * (2 * KR) + 64u * h;
+    float nout = 0.f;
+#pragma unroll
+    for (int hh = 0; hh < 4; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(cb + 16 * hh, rb);
+      TmemLd<16>::run(cb + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+      for (int i = 0; i < 16; i++) {
+        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
+        nout = fmaf(y, y, nout);
+      }
+    }
+    red_out[tid] = nout;
+    __syncthreads();
+    nout += red_out[tid ^ kTcThreads];
+    const float f = nout > 0.f ? sqrtf(pnin / nout) : 1.f;
+#pragma unroll
+    for (int hh = 0; hh < 4; hh++) {
+      uint32_t rb[16], rs[16];
+      TmemLd<16>::run(cb + 16 * hh, rb);
+      TmemLd<16>::run(cb + KR + 16 * hh, rs);
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      float4 y[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
+                           (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
+                           (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
+                           (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
+      xch.run<4>(y);
+#pragma unroll
+      for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + pbase + offset(4 * hh + q)) = y[q];
+    }
+    return true;
+  };
+
+  bool aborted = false;
+  bool prev = false;           // a tile of the previous iteration awaits its epilogue
+  uint64_t prev_base = 0;
+  float prev_nin = 0.f;
+  int it = 0;
+  long long tile = blockIdx.x;
+  // ST: tile t into the staging area (one commit group, empty past the end)
+  uint64_t sbase = 0;
+  auto stage_in = [&](long long t) {
+    const bool ok = t < p.n_tiles;
+    sbase = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
+    if (ok) {
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + sbase + offset(q));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if constexpr (ST) stage_in(tile);
+  else gather(tile);
+  for (;; tile += gridDim.x, it++) {
+    const bool have = tile < p.n_tiles;
+    const int buf = DB ? (it & 1) : 0;
+    uint64_t cur_base = 0;
+    float cur_nin = 0.f;
+    if (have) {
+      if constexpr (ST) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        const unsigned char *src = sStage + (uint32_t)tid * 16u;
+#pragma unroll
+        for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
+        base = sbase;
+        stage_in(tile + gridDim.x);  // own chunks only: refill at once
+      }
+      xch.run<NV>(v);
+      float mx = 0.f, nin = 0.f;
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+        nin = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, nin))));
+      }
+      red_in[2 * tid] = mx;
+      red_in[2 * tid + 1] = nin;
+      __syncthreads();
+      mx = fmaxf(mx, red_in[2 * (tid ^ kTcThreads)]);
+      nin += red_in[2 * (tid ^ kTcThreads) + 1];
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      const float sc = ldexpf(1.f, -e);
+      unsigned char *sA_hi = smem + (uint32_t)buf * 2u * A_BYTES;
+      unsigned char *sA_lo = sA_hi + A_BYTES;
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
+                            v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
+        uint4 hi, lo;
+        split_row(x, hi, lo);
+        *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
+        *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (tid == 0) {
+        const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
+        const uint32_t dcol = tmem + (uint32_t)buf * (2 * KR);
+#pragma unroll
+        for (int ks = 0; ks < KR / 16; ks++) {
+          const uint32_t koff = (uint32_t)ks * 2u * LBO;
+          const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+          const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+          const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+          const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+          const uint32_t acc = ks > 0 ? 1u : 0u;
+          mma_f16(dcol, dah, dbh, IDESC, acc);
+          mma_f16(dcol + KR, dah, dbl, IDESC, acc);
+          mma_f16(dcol + KR, dal, dbh, IDESC, 1u);
+        }
+        if (!p.withhold_commit) mma_commit(smem_addr(&mbar[buf]));
+      }
+      cur_base = base;
+      cur_nin = nin;
+      if constexpr (!ST) gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
+    }
+    if (DB && prev) {
+      // the previous tile (other buffer) while this one's MMAs run
+      if (!epilogue(buf ^ 1, prev_base, prev_nin)) {
+        aborted = true;
+        break;
+      }
+    }
+    if (!DB && have) {
+      // single buffer: this tile, while the next one's loads are in flight
+      if (!epilogue(buf, cur_base, cur_nin)) {
+        aborted = true;
+        break;
+      }
+    }
+    if (!have) break;
+    prev = true;
+    prev_base = cur_base;
+    prev_nin = cur_nin;
+  }
+  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (aborted) {
+    // MMAs may still be in flight: one more commit tracks all of them; wait
+    // for it (bounded) before the columns are returned
+    if (tid == 0) mma_commit(smem_addr(&mbar[2]));
+    mbar_wait(smem_addr(&mbar[2]), 0);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+}
+
+template <int K, bool ST>
+cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                      cudaStream_t s) {
+  TcXParam p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_tiles = (1ll << (n - K - b.nctrl)) / kTcThreads;
+  p.cmask = b.cmask;
+  p.nf = x.nf;
+  for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
+  for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
+  for (int j = 0; j < K - 1; j++) p.rbit[j] = x.rbit[j];
+  p.la = x.la;
+  p.nswb = x.nswb;
+  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
+  // ST: two staging areas of one tile (2^(K-1) 16-byte chunks per thread)
+  const size_t smem = tc16_smem_bytes<K>() + (ST ? 2 * (size_t)(1 << (K - 1)) * kTcThreads * 16 : 0);
+  constexpr int want = ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value;
+  static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc16x<K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc16x<K, ST>, kTcThreads, smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int tmem_cap = 512 / (4 << K);
+    per_sm = occ > want ? want : occ;
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms * per_sm;
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16x<K, ST><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
+template <bool DB, bool ST>
+cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                       cudaStream_t s) {
+  TcXParam p;
+  std::memset(&p, 0, sizeof(p));
+  p.n_tiles = (1ll << (n - 6 - b.nctrl)) / kTcThreads;
+  p.cmask = b.cmask;
+  p.nf = x.nf;
+  for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
+  for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
+  for (int j = 0; j < 4; j++) p.rbit[j] = x.rbit[j];
+  p.la = x.la;
+  p.nswb = x.nswb;
+  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
+  p.th = x.th;
+  p.withhold_commit = b.withhold_commit ? 1 : 0;
+  // one or two A buffers (hi + lo) of 64 KB, B (hi + lo) of 64 KB, ST: a
+  // 64 KB staging area
+  const size_t smem = (DB ? 4 : 2) * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2 +
+                      (ST ? (size_t)16 * 2 * kTcThreads * 16 : 0);
+  static thread_local int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc16x6<DB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (resident_ctas((const void *)k_dense_tc16x6<DB, ST>, 2 * kTcThreads, smem) < 1)
+      return cudaErrorInvalidConfiguration;
+    configured = dev;
+  }
+  long long grid = (long long)dev_info().sms;  // one CTA per SM (512 TMEM columns each)
+  if (grid > p.n_tiles) grid = p.n_tiles;
+  k_dense_tc16x6<DB, ST><<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t run_dense_tc16x(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+  TcXLayout x;
+  if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
+  if (b.k == 6) {
+    if (b.tc_prefetch == 2) return run_tc16x6<true, false>(a, n, b, x, dev_b, err, s);
+    return b.tc_xg_stage ? run_tc16x6<false, true>(a, n, b, x, dev_b, err, s)
+                         : run_tc16x6<false, false>(a, n, b, x, dev_b, err, s);
+  }
+  if (b.tc_xg_stage)
+    return b.k == 4 ? run_tc16x<4, true>(a, n, b, x, dev_b, err, s) : run_tc16x<5, true>(a, n, b, x, dev_b, err, s);
+  return b.k == 4 ? run_tc16x<4, false>(a, n, b, x, dev_b, err, s) : run_tc16x<5, false>(a, n, b, x, dev_b, err, s);
+}
+
+}  // namespace kern
+
+bool tc_exchange_pays(const Block &b) {
+  if (b.kind != BK_DENSE || b.k < 4 || b.k > 6) return false;
+  // measured on GB300 from random states at n = 28: with 5 targets the
+  // exchange kernel is ahead for every placement (5.77-6.01 vs 5.56-5.72 TB/s
+  // with at most one low target, 4.87-5.79 vs 3.21-4.96 with two or three);
+  // with 4 targets only where two or more targets lie among bits 1..3
+  // (4.89-5.34 vs 3.41-5.29 TB/s), elsewhere the plain gather is ahead
+  // (5.84-6.29 vs 5.59-5.87); with 6 targets (two threads per group) where
+  // any target lies among bits 1..3 (4.40-5.13 vs 3.17-5.02 TB/s), not for
+  // high targets (5.10-5.51 vs 5.50-5.54)
+  if (b.k == 5) return true;
+  int low = 0;
+  for (int j = 0; j < b.k; j++) low += (b.q[j] >= 1 && b.q[j] <= 3) ? 1 : 0;
+  return b.k == 6 ? low >= 1 : low >= 2;
+}
+
+bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
+  if (b.kind == BK_DENSE && b.k == 6 && !(b.cmask & 1ull)) {
+    // two threads per group: each half is a 5-target exchange over the five
+    // lower targets with the highest one fixed (like a control) per half
+    Block b5;
+    b5.kind = BK_DENSE;
+    b5.k = 5;
+    for (int j = 0; j < 5; j++) b5.q[j] = b.q[j];
+    b5.cmask = b.cmask | (1ull << b.q[5]);
+    b5.nctrl = b.nctrl + 1;
+    if (!tc_exchange_layout(n, b5, x)) return false;
+    x.th = b.q[5];
+    x.slot_mat[5] = 5;
+    return true;
+  }
+  x.th = -1;
+  if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5) || (b.cmask & 1ull)) return false;
+  const int K = b.k;
+  if (n - K - b.nctrl < 7) return false;  // whole tiles of 128 groups
+  uint64_t tmask = 0;
+  for (int j = 0; j < K; j++) tmask |= 1ull << b.q[j];
+  const uint64_t used = tmask | b.cmask;
+  uint64_t cube = tmask;  // the warp's sub-cube: targets + the five lowest free bits
+  for (int q = 0, nfree = 0; q < 64 && nfree < 5; q++)
+    if (!((used >> q) & 1)) {
+      cube |= 1ull << q;
+      nfree++;
+    }
+  if (!(cube & 1ull) || __builtin_popcountll(cube) != K + 5) return false;
+  auto is_t = [&](int q) { return ((tmask >> q) & 1) != 0; };
+  // lane bits: the five lowest bits of the sub-cube above bit 0 (longest
+  // runs per load); the rest are register bits
+  uint64_t lanes = 0;
+  for (int q = 1, nl = 0; q < 64 && nl < 5; q++)
+    if ((cube >> q) & 1) {
+      lanes |= 1ull << q;
+      nl++;
+    }
+  // targets left on lane bits once the element bit (if free) has taken the
+  // lowest one; above two, the highest of them trade places with the lowest
+  // free register bits (shorter runs per load, fewer exchanges)
+  auto lane_targets = [&]() { return __builtin_popcountll(lanes & tmask) - (is_t(0) ? 0 : 1); };
+  while (lane_targets() > 2) {
+    const uint64_t lt = lanes & tmask, fr = cube & ~lanes & ~tmask & ~1ull;
+    if (!fr) return false;
+    const int hi_t = 63 - __builtin_clzll(lt), lo_f = __builtin_ctzll(fr);
+    lanes = (lanes & ~(1ull << hi_t)) | (1ull << lo_f);
+  }
+  int nl = 0;
+  for (int q = 0; q < 64; q++)
+    if ((lanes >> q) & 1) x.lbit[nl++] = q;
+  int lpost[5];
+  for (int i = 0; i < 5; i++) lpost[i] = x.lbit[i];
+  // element bit free: exchange it with the lowest lane bit holding a target
+  // (one exists: K targets, K - 1 register bits)
+  x.la = -1;
+  int epost = 0;
+  if (!is_t(0)) {
+    for (int i = 0; i < 5 && x.la < 0; i++)
+      if (is_t(x.lbit[i])) x.la = i;
+    if (x.la < 0) return false;
+    epost = x.lbit[x.la];
+    lpost[x.la] = 0;
+  }
+  // lane bits still holding targets <-> register bits holding free bits
+  // (equally many); the latter become register bits 0, 1
+  int tl[5], ntl = 0, fr[4], nfr = 0, tr[4], ntr = 0;
+  for (int i = 0; i < 5; i++)
+    if (is_t(lpost[i])) tl[ntl++] = i;
+  for (int q = 1; q < 64; q++)
+    if (((cube & ~lanes) >> q) & 1) {
+      if (is_t(q)) {
+        if (ntr < 4) tr[ntr] = q;
+        ntr++;
+      } else {
+        if (nfr < 4) fr[nfr] = q;
+        nfr++;
+      }
+    }
+  if (ntr + nfr != K - 1 || ntl != nfr || ntl > 2) return false;
+  x.nswb = ntl;
+  int rb = 0;
+  for (int i = 0; i < nfr; i++) x.rbit[rb++] = fr[i];
+  for (int i = 0; i < ntr; i++) x.rbit[rb++] = tr[i];
+  for (int i = 0; i < ntl; i++) x.lb[i] = tl[i];
+  // the target each slot bit holds once the exchanges are done
+  int slot_phys[6];
+  slot_phys[0] = epost;
+  for (int j = 0; j < K - 1; j++) slot_phys[1 + j] = j < ntl ? lpost[tl[j]] : x.rbit[j];
+  for (int s = 0; s < K; s++) {
+    x.slot_mat[s] = -1;
+    for (int t = 0; t < K; t++)
+      if (b.q[t] == slot_phys[s]) x.slot_mat[s] = t;
+    if (x.slot_mat[s] < 0) return false;
+  }
+  const uint64_t fixedm = cube | b.cmask;
+  if (__builtin_popcountll(fixedm) > kMaxFixed) return false;
+  x.nf = 0;
+  for (int q = 0; q < 64; q++)
+    if ((fixedm >> q) & 1) x.fixed[x.nf++] = q;
+  return true;
+}
+
+}  // namespace qs
