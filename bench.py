@@ -325,7 +325,8 @@ def run_ours(args):
 # k_dense_tc16_6_n26.md, k_diag_chunk_n26.md, k_phase_n26.md, k_tile_n26.md:
 # 1026.3 / 1013.3 / 1012.2 / 1013.2 / 1012.5 MB at n=26 -> x16); absent where
 # no capture of the current kernel exists.
-TRAFFIC_PER_LAUNCH = {"k_dense_k5_tcx": 16.20e9, "k_dense_k5_tc": 16.42e9, "k_dense_k6_tc": 16.21e9, "k_diag": 16.19e9,
+TRAFFIC_PER_LAUNCH = {"k_dense_k5_tcx": 16.20e9, "k_dense_k5_tc": 16.42e9, "k_dense_k4_tc": 16.29e9,
+                      "k_dense_k6_tcx": 16.19e9, "k_dense_k6_tc": 16.21e9, "k_diag": 16.19e9,
                       "k_phase": 16.21e9, "k_tile": 16.20e9}
 
 
