@@ -862,7 +862,8 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     // per-thread gathers staged two tiles ahead by cp.async (4, 5 targets, one
     // thread per group)
     if (opts.tc_gather == 5 && b.tc_rows == 1 && (b.k == 4 || b.k == 5)) b.tc_prefetch = 3;
-    // lane-exchange gathers where the plain gather reads short runs
+    // lane-exchange gathers where they measured faster (tc_exchange_pays),
+    // or everywhere the layout allows with tc_exchange = 2
     TcXLayout xl;
     const bool xg_shape = b.k == 6 ? (b.tc_rows == 2 && !b.tc_splitk) : (b.k >= 4 && b.tc_rows == 1);
     // (6 targets with tc_gather = 4: the double-buffered exchange kernel)
