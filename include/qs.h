@@ -119,15 +119,18 @@ typedef struct {
                            (4 acts as 2 below 5 targets); 0 = 2 for 6-target blocks, else 1 */
   int tc_gather;        /* QS_TC with FP16 halves: 0 = default: lane-exchange blocks of 4, 5
                            targets stage their loads two tiles ahead in shared memory by
-                           cp.async, other blocks as 2; 1 = staged: the plain kernel copies
-                           tiles into shared memory in address order (4, 5 targets), exchange
-                           blocks as 0; 2 = per-thread gathers, next tile gathered into registers
-                           during the MMAs; 3 = per-thread gathers without that
-                           prefetch (more CTAs per SM; 1 thread per group at 4, 5 targets,
-                           2 at 6); 4 = per-thread gathers two tiles ahead (same threads; for
-                           6-target lane-exchange blocks: two tiles in flight through double-
-                           buffered operands and accumulators); 5 = per-thread gathers of 4, 5
-                           targets staged two tiles ahead in shared memory by cp.async */
+                           cp.async, other blocks as 2; 1 = staged: the thread-per-group kernel
+                           copies tiles into shared memory in address order (4, 5 targets),
+                           lane-exchange blocks stage by cp.async (6 targets: one tile ahead
+                           through a 64 KB area); 2 = per-thread gathers, next tile gathered
+                           into registers during the MMAs (lane-exchange blocks too); 3 =
+                           per-thread gathers without that prefetch (more CTAs per SM; 1 thread
+                           per group at 4, 5 targets, 2 at 6); 4 = per-thread gathers two tiles
+                           ahead (same threads; for 6-target lane-exchange blocks: two tiles in
+                           flight through double-buffered operands and accumulators); 5 = the
+                           thread-per-group kernel's gathers of 4, 5 targets staged two tiles
+                           ahead in shared memory by cp.async. Only 0 is tuned; the others
+                           measured slower on GB300 and stay for comparison */
   int fuse_lookahead;   /* fusion: where a gate could join several blocks or open a new one,
                            each choice is followed by this many gates of first-fit placement
                            and the one leaving the fewest blocks is taken; 0 = first fit
