@@ -115,36 +115,24 @@ typedef struct {
   int tile_bits;        /* QS_TILE: qubits per shared-memory tile, 0 = 64 KiB of amplitudes
                            (13 for c64, 12 for c128); 8..14 c64, 8..13 c128 */
   int tile_k;           /* QS_TILE: fusion width inside a tile, 0 = 3; 1..4 */
-  int tc_row_threads;   /* QS_TC with FP16 halves: threads sharing one group (row): 1, 2 or 4
-                           (4 acts as 2 below 5 targets); 0 = 2 for 6-target blocks, else 1 */
-  int tc_gather;        /* QS_TC with FP16 halves: 0 = default: lane-exchange blocks of 4, 5
-                           targets stage their loads two tiles ahead in shared memory by
-                           cp.async, other blocks as 2; 1 = staged: the thread-per-group kernel
-                           copies tiles into shared memory in address order (4, 5 targets),
-                           lane-exchange blocks stage by cp.async (6 targets: one tile ahead
-                           through a 64 KB area); 2 = per-thread gathers, next tile gathered
-                           into registers during the MMAs (lane-exchange blocks too); 3 =
-                           per-thread gathers without that prefetch (more CTAs per SM; 1 thread
-                           per group at 4, 5 targets, 2 at 6); 4 = per-thread gathers two tiles
-                           ahead (same threads; for 6-target lane-exchange blocks: two tiles in
-                           flight through double-buffered operands and accumulators); 5 = the
-                           thread-per-group kernel's gathers of 4, 5 targets staged two tiles
-                           ahead in shared memory by cp.async. Only 0 is tuned; the others
-                           measured slower on GB300 and stay for comparison */
   int fuse_lookahead;   /* fusion: where a gate could join several blocks or open a new one,
                            each choice is followed by this many gates of first-fit placement
                            and the one leaving the fewest blocks is taken; 0 = first fit
                            (qs_default_opts: 60) */
   int no_shuffles;      /* 1: CUDA-core blocks whose targets cover bits 1, 2, 3 (bit 0 free) keep
                            the thread-per-group kernel instead of warp-wide loads and shuffles (c64) */
-  int tc_split_k;       /* 6-target tensor-core blocks: 1 = K in two halves through 96 KB of shared
-                           memory (two CTAs per SM), 2 = whole K (128 KB, one CTA); 0 = default */
-  int tc_exchange;      /* 4- to 6-target tensor-core blocks (FP16 halves):
-                           0 = lane-exchange gathers where they measured faster (every 5-target
-                           block, 4-target blocks with two or more targets among bits 1..3,
-                           6-target blocks (two threads per group) with one or more);
-                           1 = never; 2 = wherever the layout allows (bit 0 not a control,
-                           whole tiles of 128 groups) */
+  int tc_exchange;      /* 4- to 6-target tensor-core blocks (FP16 halves): the thread-per-group
+                           kernel (each thread gathers its own group) or the lane-exchange kernel
+                           (a warp loads its groups' sub-cube in address order and hands each
+                           lane its group by warp shuffles):
+                           0 = lane exchange where it measured faster (every 5-target block,
+                           4-target blocks with two or more targets among bits 1..3, 6-target
+                           blocks with one or more); 1 = never; 2 = wherever the layout allows
+                           (bit 0 not a control, whole tiles of 128 groups) */
+  int tc_max_ctas;      /* test hook, 0 in normal use: at most this many CTAs per tensor-core
+                           launch (normally one wave of resident CTAs, no more than there are
+                           tiles), so that every CTA loops over several tiles even on a small
+                           state; the block records report tiles and CTAs */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);
@@ -232,6 +220,10 @@ typedef struct {
   double bytes;      /* algorithmic bytes: 2 x amplitudes changed x amplitude size */
   double t_start_ms; /* start relative to the first block (QS_PROFILE), else -1 */
   double ms;         /* device time (QS_PROFILE), else -1 */
+  int64_t tiles;     /* tensor-core blocks of an apply call: tiles of 128 groups; else 0 */
+  int32_t ctas;      /* tensor-core blocks of an apply call: CTAs launched (each loops over
+                        tiles ctas apart); else 0 */
+  int32_t reserved;
 } qs_block_record;
 
 typedef struct {

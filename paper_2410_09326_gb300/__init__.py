@@ -64,9 +64,8 @@ class qs_opts(ctypes.Structure):
                 ("diag_max", ctypes.c_int), ("threads", ctypes.c_int),
                 ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
                 ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
-                ("tile_k", ctypes.c_int), ("tc_row_threads", ctypes.c_int),
-                ("tc_gather", ctypes.c_int), ("fuse_lookahead", ctypes.c_int),
-                ("no_shuffles", ctypes.c_int), ("tc_split_k", ctypes.c_int), ("tc_exchange", ctypes.c_int)]
+                ("tile_k", ctypes.c_int), ("fuse_lookahead", ctypes.c_int),
+                ("no_shuffles", ctypes.c_int), ("tc_exchange", ctypes.c_int), ("tc_max_ctas", ctypes.c_int)]
 
 
 class qs_class_table(ctypes.Structure):
@@ -87,7 +86,8 @@ class qs_block_record(ctypes.Structure):
                 ("qubits", ctypes.c_int8 * QS_MAX_DIAG), ("meta", ctypes.c_uint8),
                 ("op", ctypes.c_uint8), ("n_gates", ctypes.c_int32), ("cmask", ctypes.c_uint64),
                 ("bytes", ctypes.c_double),
-                ("t_start_ms", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("t_start_ms", ctypes.c_double), ("ms", ctypes.c_double),
+                ("tiles", ctypes.c_int64), ("ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class qs_exchange_layout(ctypes.Structure):

@@ -390,7 +390,8 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   for (size_t i = 0; i < plan.size(); i++) {
     const Block &b = plan[i];
     const void *dm = mat_off[i] == (size_t)-1 ? nullptr : (const unsigned char *)st->d_mats + mat_off[i];
-    e = launch_block_with_matrix(st->amps, st->n, c128, b, dm, st->d_err, st->stream, o.threads);
+    LaunchShape shape;
+    e = launch_block_with_matrix(st->amps, st->n, c128, b, dm, st->d_err, st->stream, o.threads, &shape);
     if (e != cudaSuccess) return cuda_fail(st, e, "qs_apply_circuit launch");
     if (prof) {
       e = cudaEventRecord(st->events[i + 1], st->stream);
@@ -398,6 +399,8 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
     }
     qs_block_record r;
     fill_record(b, (int)i, st->n, ab, r);
+    r.tiles = shape.tiles;
+    r.ctas = shape.ctas;
     st->rec_class.push_back(block_class(b));
     st->h2d_bytes += (double)block_param_bytes(b, c128);
     st->recs.push_back(r);

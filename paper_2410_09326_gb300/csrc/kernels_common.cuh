@@ -204,12 +204,14 @@ cudaError_t run_dense_smem(T *a, int n, const Block &b, const T *dev_mat, cudaSt
 // error word set to 1 when a bounded wait expires.
 size_t tc_b_floats(int k);
 void tc_build_b(const Block &b, float *out);
-cudaError_t run_dense_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s);
+cudaError_t run_dense_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                         LaunchShape *shape);
 // FP16-operand variant (tc16.cu), k = 4..6: dev_b holds tc16_b_bytes(k) bytes
 // written by tc16_build_b.
 size_t tc16_b_bytes(int k);
 void tc16_build_b(const Block &b, void *out);
-cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s);
+cudaError_t run_dense_tc16(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                           LaunchShape *shape);
 
 // Cache-blocked passes (tile.cu): a BK_TILE block's descriptor (header,
 // member matrices and tables, member descriptors) lives in device memory.

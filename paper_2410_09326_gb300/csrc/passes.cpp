@@ -674,20 +674,12 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     return QS_EUNSUPPORTED;
   }
   int D = std::max(1, std::min(opts.diag_max, QS_MAX_DIAG));
-  if (opts.tc_split_k < 0 || opts.tc_split_k > 2) {
-    err = "opts.tc_split_k out of range (0..2)";
-    return QS_EINVAL;
-  }
   if (opts.tc_exchange < 0 || opts.tc_exchange > 2) {
     err = "opts.tc_exchange out of range (0..2)";
     return QS_EINVAL;
   }
-  if (opts.tc_gather < 0 || opts.tc_gather > 5) {
-    err = "opts.tc_gather out of range (0..5)";
-    return QS_EINVAL;
-  }
-  if (opts.tc_row_threads < 0 || opts.tc_row_threads == 3 || opts.tc_row_threads > 4) {
-    err = "opts.tc_row_threads must be 0, 1, 2 or 4";
+  if (opts.tc_max_ctas < 0) {
+    err = "opts.tc_max_ctas must not be negative";
     return QS_EINVAL;
   }
   if (flags & QS_TILE) {
@@ -849,34 +841,14 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   for (Block &b : plan) {
     b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= (tf32 ? 5 : 6);
     b.tc_tf32 = b.tc && tf32;
-    // two threads per group only pay off at k = 6, where one thread per
-    // group would need more registers than exist (measured on GB300)
-    b.tc_rows = opts.tc_row_threads != 0 ? opts.tc_row_threads : (b.k >= 6 ? 2 : 1);
-    if (b.tc_rows == 4 && b.k < 5) b.tc_rows = 2;  // a thread converts at least 4 amplitudes
-    // staging tiles through shared memory measured slower than per-thread
-    // gathers on GB300 (4.0 vs 6.3 TB/s at 5 targets), so it is opt-in
     b.shuffles = opts.no_shuffles == 0;
-    b.tc_splitk = b.tc && b.k == 6 && b.tc_rows == 2 && opts.tc_split_k == 1;
-    b.tc_staged = b.tc && !tf32 && opts.tc_gather == 1;
-    b.tc_prefetch = opts.tc_gather == 3 ? 0 : (opts.tc_gather == 4 ? 2 : 1);
-    // per-thread gathers staged two tiles ahead by cp.async (4, 5 targets, one
-    // thread per group)
-    if (opts.tc_gather == 5 && b.tc_rows == 1 && (b.k == 4 || b.k == 5)) b.tc_prefetch = 3;
     // lane-exchange gathers where they measured faster (tc_exchange_pays),
     // or everywhere the layout allows with tc_exchange = 2
     TcXLayout xl;
-    const bool xg_shape = b.k == 6 ? (b.tc_rows == 2 && !b.tc_splitk) : (b.k >= 4 && b.tc_rows == 1);
-    // (6 targets with tc_gather = 4: the double-buffered exchange kernel)
-    const bool xg_pf = b.tc_prefetch == 1 || (b.k == 6 && b.tc_prefetch == 2);
-    b.tc_xg = b.tc && !tf32 && xg_shape && xg_pf && opts.tc_exchange != 1 &&
-              (opts.tc_exchange == 2 || tc_exchange_pays(b)) && tc_exchange_layout(n, b, xl);
-    // the 4/5-target exchange kernel stages its loads two tiles ahead in shared
-    // memory unless per-thread register gathers are asked for: measured on
-    // GB300 from random states at n = 28, 5 targets 5102-6302 GB/s staged vs
-    // 5177-5978 in registers, 4 targets with low targets 5753-6100 vs 5259-5521
-    // (6 targets: staged only when asked for with tc_gather = 1, measured slower)
-    b.tc_xg_stage = b.tc_xg && (b.k <= 5 ? opts.tc_gather != 2 : opts.tc_gather == 1 && b.tc_prefetch == 1);
+    b.tc_xg = b.tc && !tf32 && opts.tc_exchange != 1 && (opts.tc_exchange == 2 || tc_exchange_pays(b)) &&
+              tc_exchange_layout(n, b, xl);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
+    b.tc_max_ctas = b.tc ? opts.tc_max_ctas : 0;
   }
   return QS_OK;
 }

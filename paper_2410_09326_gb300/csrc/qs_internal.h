@@ -59,14 +59,10 @@ struct Block {
   int meta = 4;                   // 0 one-qubit, 1 two-qubit, 3 swap, 4 fused
   bool tc = false;
   bool tc_tf32 = false;           // tensor-core operands: 3 x TF32 instead of 2 x FP16
-  int tc_rows = 1;                // FP16 tensor-core kernel: threads per group (1 or 2)
-  bool tc_staged = false;         // FP16 tensor-core kernel: tiles staged through shared memory
-  int tc_prefetch = 1;            // FP16 tensor-core kernel: tiles gathered ahead (0, 1, 2)
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
-  bool tc_splitk = false;         // 6-target tensor-core blocks: K in two halves (two CTAs per SM)
   bool tc_xg = false;             // 4..6-target tensor-core blocks: lane-exchange gathers (tc16x.cu)
-  bool tc_xg_stage = false;       // exchange kernel (4, 5 targets): loads staged by cp.async, two tiles ahead
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
+  int tc_max_ctas = 0;            // test hook (qs_opts.tc_max_ctas): cap on tensor-core CTAs
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,
   // dense targets inside the tile, diagonal qubits and controls anywhere
@@ -171,6 +167,13 @@ bool dev_refused_by_budget();
 // ---------------------------------------------------------------------------
 // Kernel launchers (kernels.cu). All asynchronous on `s`.
 // ---------------------------------------------------------------------------
+// Launch shape of a tensor-core block: tiles of 128 groups and CTAs launched
+// (each CTA loops over tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
+struct LaunchShape {
+  long long tiles = 0;
+  int ctas = 0;
+};
+
 struct DevInfo {
   int sms = 0;
   int max_threads_per_sm = 0;
@@ -187,9 +190,10 @@ void fill_dev_matrix(const Block &b, bool c128, void *host_out);
 // Bytes of gate data one block ships to the device: its kernel parameters
 // (matrix or phase table included) plus any matrix upload.
 size_t block_param_bytes(const Block &b, bool c128);
-// err: device error word for kernels with bounded waits (tensor-core path).
+// err: device error word for kernels with bounded waits (tensor-core path);
+// shape (may be null) receives a tensor-core launch's tiles and CTAs.
 cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &b, const void *dev_mat,
-                                     int *err, cudaStream_t s, int threads);
+                                     int *err, cudaStream_t s, int threads, LaunchShape *shape = nullptr);
 cudaError_t launch_permute(void *amps, int n, bool c128, int a, int b, cudaStream_t s);
 cudaError_t launch_set_basis(void *amps, int n, bool c128, uint64_t idx, cudaStream_t s);
 

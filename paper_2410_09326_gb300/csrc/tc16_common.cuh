@@ -58,7 +58,8 @@ template <int K> size_t tc16_smem_bytes() {
 
 // The lane-exchange kernels (tc16x.cu) for a block the planner marked for
 // them (b.tc_xg); B must have been built in slot order (tc16_build_b does).
-cudaError_t run_dense_tc16x(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s);
+cudaError_t run_dense_tc16x(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                            LaunchShape *shape);
 
 }  // namespace kern
 }  // namespace qs

@@ -97,24 +97,17 @@ struct LaneExchange {
   }
 };
 
-// Resident CTAs per SM of the exchange kernel (registers per thread follow).
-// Measured on GB300 from random states at n = 28: spill-free registers beat
-// more resident CTAs -- 5 targets at 2 CTAs (237 registers) ran 5413-6024
-// GB/s, at 3 (168, spilling) 5386-5913, at 4 (128) 4053-4119; 4 targets at
-// 3 CTAs (153 registers) 5508-5858, at 4 (128, spilling) 5344-5728.
-template <int K> struct Tc16xOcc {
-  static constexpr int value = K <= 4 ? 3 : 2;
-};
+// The loads go to shared memory by cp.async, two tiles ahead (two staging
+// areas); each thread copies and later reads back exactly its own 16-byte
+// chunks (consecutive threads, consecutive chunks), so no barrier guards the
+// staging areas. Without registers held for tiles in flight the SM keeps four
+// tiles (128 KB at 5 targets) on the way: the n = 30 benchmark step's
+// dominant kernel went from 5.95 (one tile ahead in registers) to 6.36 TB/s
+// on GB300. Resident CTAs per SM: 4 (K = 4), 2 (K = 5).
+template <int K> constexpr int tc16x_occ() { return K <= 4 ? 4 : 2; }
 
-// ST (the default): the loads go to shared memory by cp.async, two tiles
-// ahead (two staging areas), instead of one tile ahead into registers; each
-// thread copies and later reads back exactly its own 16-byte chunks
-// (consecutive threads, consecutive chunks), so no barrier guards the staging
-// areas. Without registers held for tiles in flight the SM keeps four tiles
-// (128 KB at 5 targets) on the way instead of two: 5.95 -> 6.36 TB/s in the
-// n = 30 benchmark step on GB300.
-template <int K, bool ST>
-__global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value)
+template <int K>
+__global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                   int *__restrict__ err) {
   constexpr int D = 1 << K;
@@ -133,7 +126,7 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
   unsigned char *sA_hi = smem;
   unsigned char *sA_lo = smem + A_BYTES;
   unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
-  unsigned char *sStage = sB + 2 * B_BYTES;  // ST: two staging areas
+  unsigned char *sStage = sB + 2 * B_BYTES;  // two staging areas
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
 
@@ -181,14 +174,7 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
   float4 v[NV];
   uint64_t base = 0;
   bool valid = false;
-  auto gather = [&](long long t) {
-    valid = t < p.n_tiles;  // uniform over the CTA
-    base = valid ? (insert_zeros((uint64_t)(t * 4 + warp), p.fixed, p.nf) | p.cmask) : 0;
-#pragma unroll
-    for (int r = 0; r < NV; r++)
-      v[r] = valid ? *reinterpret_cast<const float4 *>(a + base + offset(r)) : make_float4(0.f, 0.f, 0.f, 0.f);
-  };
-  // ST: tile t into staging area u (one commit group per tile, empty past the end)
+  // tile t into staging area u (one commit group per tile, empty past the end)
   uint64_t sbase0 = 0, sbase1 = 0;
   bool svalid0 = false, svalid1 = false;
   auto stage_in = [&](long long t, int u) {
@@ -208,15 +194,11 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  if constexpr (ST) {
-    stage_in(tile, 0);
-    stage_in(tile + gridDim.x, 1);
-  } else {
-    gather(tile);
-  }
+  stage_in(tile, 0);
+  stage_in(tile + gridDim.x, 1);
 
   for (int it = 0; tile < p.n_tiles; tile += gridDim.x, it++) {
-    if constexpr (ST) {
+    {
       // this tile's group has landed once at most the next one is pending
       asm volatile("cp.async.wait_group 1;" ::: "memory");
       const int u = it & 1;
@@ -267,10 +249,9 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
     }
     const uint64_t cur_base = base;
     const bool cur_valid = valid;
-    // ST: refill the area just read (this thread's own chunks). Refilling it
+    // refill the area just read (this thread's own chunks). Refilling it
     // right after the read instead measured 0.5-1.8% slower on GB300.
-    if constexpr (ST) stage_in(tile + 2 * (long long)gridDim.x, it & 1);
-    else gather(tile + gridDim.x);  // next tile, in flight during the MMAs
+    stage_in(tile + 2 * (long long)gridDim.x, it & 1);
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -315,7 +296,7 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
       }
     }
   }
-  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
+  asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
@@ -331,22 +312,9 @@ __global__ void __launch_bounds__(kTcThreads, ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K
 // each exactly as a 5-target exchange warp (the highest target fixed per
 // half; slot bit 5 = the highest target). The row's scale and norms are
 // combined over the two halves through shared memory. The 6-target operands
-// fill an SM with one CTA, which idles while its MMAs run (about a fifth of
-// a tile); DB = true double-buffers the A operands (64 KB per tile) and the
-// TMEM accumulators (256 columns per tile) so that the MMAs of tile i run
-// while the CTA stores tile i - 1. Measured on GB300 that is slower (4.08-4.63
-// vs 4.40-5.51 TB/s): the next tile's loads then have only the stores to
-// arrive in, instead of the MMAs and the stores, and one CTA cannot hide the
-// rest of their latency. DB = false keeps the order of the other kernels.
-// ST (single buffer; opt-in, opts.tc_gather = 1): the loads go to a 64 KB
-// shared-memory staging area by cp.async; a thread refills its own chunks
-// right after reading them back at the top of a tile, so the next tile is in
-// flight through the whole tile (register gathers can only be issued once
-// the convert has freed the registers). Measured on GB300 it is 4-8% slower
-// than the register gathers (4.08-5.19 vs 4.41-5.51 TB/s): with one CTA per
-// SM the copies' issue and the shared-memory round trip cost more than the
-// longer flight gains.
-template <bool DB, bool ST>
+// (A and B, hi and lo: 128 KB) fill an SM with one CTA; the next tile is
+// gathered into registers while the current tile's MMAs run and its results
+// are stored.
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
@@ -354,20 +322,18 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   constexpr int NV = 16;        // 16-byte registers per thread (32 amplitudes)
   constexpr int RB = 4;         // register bits
   constexpr int KR = 128;       // real K = N
-  constexpr uint32_t A_BYTES = 128u * KR * 2u;     // one of hi / lo, one tile
+  constexpr uint32_t A_BYTES = 128u * KR * 2u;     // one of hi / lo
   constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
   constexpr uint32_t SBO = (KR / 8) * 128u;
   constexpr uint32_t LBO = 128u;
-  constexpr uint32_t NCOLS = 512;                  // two tiles x (large + small)
+  constexpr uint32_t NCOLS = 256;                  // large + small products
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  static_assert(!(DB && ST), "staging keeps one A buffer");
-  // A of buffer u: hi at u * 2 A_BYTES, lo after it; B hi/lo after the
-  // buffers; ST: the staging area after B
-  unsigned char *sB = smem + (DB ? 4 : 2) * A_BYTES;
-  unsigned char *sStage = sB + 2 * B_BYTES;
-  __shared__ __align__(8) uint64_t mbar[3];  // per buffer; [2] for the final drain
+  unsigned char *sA_hi = smem;
+  unsigned char *sA_lo = smem + A_BYTES;
+  unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ float red_in[2 * NT];
   __shared__ float red_out[NT];
@@ -384,13 +350,15 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int u = 0; u < 3; u++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[u])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
+  const uint32_t mbar_a = smem_addr(&mbar);
+  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
   const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
   const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
   const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -421,18 +389,66 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       v[q] = ok ? *reinterpret_cast<const float4 *>(a + base + offset(q)) : make_float4(0.f, 0.f, 0.f, 0.f);
   };
 
-  uint32_t ph0 = 0, ph1 = 0;   // parity each buffer's barrier waits for next
-  // wait for the MMAs of the tile in buffer pb, store it; false: timed out
-  auto epilogue = [&](int pb, uint64_t pbase, float pnin) -> bool {
-    const bool ok = mbar_wait(smem_addr(&mbar[pb]), pb ? ph1 : ph0);
-    if (pb) ph1 ^= 1;
-    else ph0 ^= 1;
+  uint32_t phase = 0;
+  bool aborted = false;
+  long long tile = blockIdx.x;
+  gather(tile);
+  for (; tile < p.n_tiles; tile += gridDim.x) {
+    xch.run<NV>(v);
+    float mx = 0.f, nin = 0.f;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+      nin = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, nin))));
+    }
+    red_in[2 * tid] = mx;
+    red_in[2 * tid + 1] = nin;
+    __syncthreads();
+    mx = fmaxf(mx, red_in[2 * (tid ^ kTcThreads)]);
+    nin += red_in[2 * (tid ^ kTcThreads) + 1];
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);
+    const float sc = ldexpf(1.f, -e);
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
+                          v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
+      uint4 hi, lo;
+      split_row(x, hi, lo);
+      *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
+      *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < KR / 16; ks++) {
+        const uint32_t koff = (uint32_t)ks * 2u * LBO;
+        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
+        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
+        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        mma_f16(tmem, dah, dbh, IDESC, acc);
+        mma_f16(tmem + KR, dah, dbl, IDESC, acc);
+        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+      }
+      if (!p.withhold_commit) mma_commit(mbar_a);
+    }
+    const uint64_t cur_base = base;
+    const float cur_nin = nin;
+    gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
+    const bool ok = mbar_wait(mbar_a, phase);
+    phase ^= 1;
     if (!__syncthreads_and(ok)) {
       if (tid == 0) atomicExch(err, 1);
-      return false;
+      aborted = true;
+      break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t cb = lane_base + (uint32_t)pb * (2 * KR) + 64u * h;
+    const uint32_t cb = lane_base + 64u * h;
     float nout = 0.f;
 #pragma unroll
     for (int hh = 0; hh < 4; hh++) {
@@ -449,7 +465,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     red_out[tid] = nout;
     __syncthreads();
     nout += red_out[tid ^ kTcThreads];
-    const float f = nout > 0.f ? sqrtf(pnin / nout) : 1.f;
+    const float f = nout > 0.f ? sqrtf(cur_nin / nout) : 1.f;
 #pragma unroll
     for (int hh = 0; hh < 4; hh++) {
       uint32_t rb[16], rs[16];
@@ -465,216 +481,101 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
                            (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
       xch.run<4>(y);
 #pragma unroll
-      for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + pbase + offset(4 * hh + q)) = y[q];
+      for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
     }
-    return true;
-  };
-
-  bool aborted = false;
-  bool prev = false;           // a tile of the previous iteration awaits its epilogue
-  uint64_t prev_base = 0;
-  float prev_nin = 0.f;
-  int it = 0;
-  long long tile = blockIdx.x;
-  // ST: tile t into the staging area (one commit group, empty past the end)
-  uint64_t sbase = 0;
-  auto stage_in = [&](long long t) {
-    const bool ok = t < p.n_tiles;
-    sbase = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
-    if (ok) {
-      const uint32_t dst = smem_addr(sStage) + (uint32_t)tid * 16u;
-#pragma unroll
-      for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + sbase + offset(q));
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  if constexpr (ST) stage_in(tile);
-  else gather(tile);
-  for (;; tile += gridDim.x, it++) {
-    const bool have = tile < p.n_tiles;
-    const int buf = DB ? (it & 1) : 0;
-    uint64_t cur_base = 0;
-    float cur_nin = 0.f;
-    if (have) {
-      if constexpr (ST) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        const unsigned char *src = sStage + (uint32_t)tid * 16u;
-#pragma unroll
-        for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
-        base = sbase;
-        stage_in(tile + gridDim.x);  // own chunks only: refill at once
-      }
-      xch.run<NV>(v);
-      float mx = 0.f, nin = 0.f;
-#pragma unroll
-      for (int q = 0; q < NV; q++) {
-        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
-        nin = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, nin))));
-      }
-      red_in[2 * tid] = mx;
-      red_in[2 * tid + 1] = nin;
-      __syncthreads();
-      mx = fmaxf(mx, red_in[2 * (tid ^ kTcThreads)]);
-      nin += red_in[2 * (tid ^ kTcThreads) + 1];
-      int e = 0;
-      if (mx > 0.f) frexpf(mx, &e);
-      const float sc = ldexpf(1.f, -e);
-      unsigned char *sA_hi = smem + (uint32_t)buf * 2u * A_BYTES;
-      unsigned char *sA_lo = sA_hi + A_BYTES;
-#pragma unroll
-      for (int c = 0; c < 8; c++) {
-        const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
-                            v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
-        uint4 hi, lo;
-        split_row(x, hi, lo);
-        *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
-        *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      if (tid == 0) {
-        const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
-        const uint32_t dcol = tmem + (uint32_t)buf * (2 * KR);
-#pragma unroll
-        for (int ks = 0; ks < KR / 16; ks++) {
-          const uint32_t koff = (uint32_t)ks * 2u * LBO;
-          const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
-          const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
-          const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
-          const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
-          const uint32_t acc = ks > 0 ? 1u : 0u;
-          mma_f16(dcol, dah, dbh, IDESC, acc);
-          mma_f16(dcol + KR, dah, dbl, IDESC, acc);
-          mma_f16(dcol + KR, dal, dbh, IDESC, 1u);
-        }
-        if (!p.withhold_commit) mma_commit(smem_addr(&mbar[buf]));
-      }
-      cur_base = base;
-      cur_nin = nin;
-      if constexpr (!ST) gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
-    }
-    if (DB && prev) {
-      // the previous tile (other buffer) while this one's MMAs run
-      if (!epilogue(buf ^ 1, prev_base, prev_nin)) {
-        aborted = true;
-        break;
-      }
-    }
-    if (!DB && have) {
-      // single buffer: this tile, while the next one's loads are in flight
-      if (!epilogue(buf, cur_base, cur_nin)) {
-        aborted = true;
-        break;
-      }
-    }
-    if (!have) break;
-    prev = true;
-    prev_base = cur_base;
-    prev_nin = cur_nin;
   }
-  if constexpr (ST) asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
     // MMAs may still be in flight: one more commit tracks all of them; wait
     // for it (bounded) before the columns are returned
-    if (tid == 0) mma_commit(smem_addr(&mbar[2]));
-    mbar_wait(smem_addr(&mbar[2]), 0);
+    if (tid == 0) mma_commit(mbar_a);
+    mbar_wait(mbar_a, phase ^ 1);
   }
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-template <int K, bool ST>
-cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
-                      cudaStream_t s) {
-  TcXParam p;
+void fill_xparam(int K, int n, const Block &b, const TcXLayout &x, TcXParam &p) {
   std::memset(&p, 0, sizeof(p));
   p.n_tiles = (1ll << (n - K - b.nctrl)) / kTcThreads;
   p.cmask = b.cmask;
   p.nf = x.nf;
   for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
   for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
-  for (int j = 0; j < K - 1; j++) p.rbit[j] = x.rbit[j];
-  p.la = x.la;
-  p.nswb = x.nswb;
-  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
-  p.withhold_commit = b.withhold_commit ? 1 : 0;
-  // ST: two staging areas of one tile (2^(K-1) 16-byte chunks per thread)
-  const size_t smem = tc16_smem_bytes<K>() + (ST ? 2 * (size_t)(1 << (K - 1)) * kTcThreads * 16 : 0);
-  constexpr int want = ST ? (K <= 4 ? 4 : 2) : Tc16xOcc<K>::value;
-  static thread_local int configured = -1;
-  static thread_local int per_sm = 1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (configured != dev) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_dense_tc16x<K, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16x<K, ST>, kTcThreads, smem);
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int tmem_cap = 512 / (4 << K);
-    per_sm = occ > want ? want : occ;
-    if (per_sm > tmem_cap) per_sm = tmem_cap;
-    configured = dev;
-  }
-  long long grid = (long long)dev_info().sms * per_sm;
-  if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16x<K, ST><<<(int)grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
-  return cudaGetLastError();
-}
-
-template <bool DB, bool ST>
-cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
-                       cudaStream_t s) {
-  TcXParam p;
-  std::memset(&p, 0, sizeof(p));
-  p.n_tiles = (1ll << (n - 6 - b.nctrl)) / kTcThreads;
-  p.cmask = b.cmask;
-  p.nf = x.nf;
-  for (int i = 0; i < x.nf; i++) p.fixed[i] = x.fixed[i];
-  for (int i = 0; i < 5; i++) p.lbit[i] = x.lbit[i];
-  for (int j = 0; j < 4; j++) p.rbit[j] = x.rbit[j];
+  for (int j = 0; j < (K == 6 ? 4 : K - 1); j++) p.rbit[j] = x.rbit[j];
   p.la = x.la;
   p.nswb = x.nswb;
   for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
   p.th = x.th;
   p.withhold_commit = b.withhold_commit ? 1 : 0;
-  // one or two A buffers (hi + lo) of 64 KB, B (hi + lo) of 64 KB, ST: a
-  // 64 KB staging area
-  const size_t smem = (DB ? 4 : 2) * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2 +
-                      (ST ? (size_t)16 * 2 * kTcThreads * 16 : 0);
+}
+
+template <int K>
+cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                      cudaStream_t s, LaunchShape *shape) {
+  TcXParam p;
+  fill_xparam(K, n, b, x, p);
+  // two staging areas of one tile (2^(K-1) 16-byte chunks per thread)
+  const size_t smem = tc16_smem_bytes<K>() + 2 * (size_t)(1 << (K - 1)) * kTcThreads * 16;
+  static thread_local int configured = -1;
+  static thread_local int per_sm = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int occ = resident_ctas((const void *)k_dense_tc16x<K>, kTcThreads, smem);
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int tmem_cap = 512 / (4 << K);
+    per_sm = occ > tc16x_occ<K>() ? tc16x_occ<K>() : occ;
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    configured = dev;
+  }
+  const int grid = tc_grid((long long)dev_info().sms * per_sm, p.n_tiles, b.tc_max_ctas);
+  if (shape) {
+    shape->tiles = p.n_tiles;
+    shape->ctas = grid;
+  }
+  k_dense_tc16x<K><<<grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  return cudaGetLastError();
+}
+
+cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, const void *dev_b, int *err,
+                       cudaStream_t s, LaunchShape *shape) {
+  TcXParam p;
+  fill_xparam(6, n, b, x, p);
+  // A (hi + lo) of 64 KB, B (hi + lo) of 64 KB
+  const size_t smem = 2 * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
   static thread_local int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_dense_tc16x6<DB, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (resident_ctas((const void *)k_dense_tc16x6<DB, ST>, 2 * kTcThreads, smem) < 1)
-      return cudaErrorInvalidConfiguration;
+    if (resident_ctas((const void *)k_dense_tc16x6, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
     configured = dev;
   }
-  long long grid = (long long)dev_info().sms;  // one CTA per SM (512 TMEM columns each)
-  if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc16x6<DB, ST><<<(int)grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  const int grid = tc_grid((long long)dev_info().sms, p.n_tiles, b.tc_max_ctas);  // one CTA per SM
+  if (shape) {
+    shape->tiles = p.n_tiles;
+    shape->ctas = grid;
+  }
+  k_dense_tc16x6<<<grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t run_dense_tc16x(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+cudaError_t run_dense_tc16x(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                            LaunchShape *shape) {
   TcXLayout x;
   if (!tc_exchange_layout(n, b, x)) return cudaErrorInvalidValue;
-  if (b.k == 6) {
-    if (b.tc_prefetch == 2) return run_tc16x6<true, false>(a, n, b, x, dev_b, err, s);
-    return b.tc_xg_stage ? run_tc16x6<false, true>(a, n, b, x, dev_b, err, s)
-                         : run_tc16x6<false, false>(a, n, b, x, dev_b, err, s);
+  switch (b.k) {
+    case 4: return run_tc16x<4>(a, n, b, x, dev_b, err, s, shape);
+    case 5: return run_tc16x<5>(a, n, b, x, dev_b, err, s, shape);
+    case 6: return run_tc16x6(a, n, b, x, dev_b, err, s, shape);
+    default: return cudaErrorInvalidValue;
   }
-  if (b.tc_xg_stage)
-    return b.k == 4 ? run_tc16x<4, true>(a, n, b, x, dev_b, err, s) : run_tc16x<5, true>(a, n, b, x, dev_b, err, s);
-  return b.k == 4 ? run_tc16x<4, false>(a, n, b, x, dev_b, err, s) : run_tc16x<5, false>(a, n, b, x, dev_b, err, s);
 }
 
 }  // namespace kern

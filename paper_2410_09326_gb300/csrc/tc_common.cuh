@@ -89,6 +89,15 @@ template <> struct TmemLd<64> {
   }
 };
 
+// CTAs of a tensor-core launch: one wave of resident CTAs (`wave`), no more
+// than there are tiles, and no more than max_ctas when that is positive (a
+// test hook that makes every CTA loop over several tiles).
+inline int tc_grid(long long wave, long long tiles, int max_ctas) {
+  long long g = wave < tiles ? wave : tiles;
+  if (max_ctas > 0 && g > max_ctas) g = max_ctas;
+  return g < 1 ? 1 : (int)g;
+}
+
 struct TcParam {
   long long n_groups;
   long long n_tiles;

@@ -324,7 +324,8 @@ template <int K> size_t tc_smem_bytes() {
 }
 
 template <int K, bool SPLIT, bool RENORM>
-cudaError_t run_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+cudaError_t run_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                   LaunchShape *shape) {
   TcParam p;
   p.n_groups = 1ll << (n - K - b.nctrl);
   p.n_tiles = (p.n_groups + kTcThreads - 1) / kTcThreads;
@@ -348,9 +349,12 @@ cudaError_t run_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err
     per_sm = occ > TcOcc<K>::value ? TcOcc<K>::value : occ;
     configured = dev;
   }
-  long long grid = (long long)dev_info().sms * per_sm;
-  if (grid > p.n_tiles) grid = p.n_tiles;
-  k_dense_tc<K, SPLIT, RENORM><<<(int)grid, kTcThreads, smem, s>>>(a, (const float4 *)dev_b, p, err);
+  const int grid = tc_grid((long long)dev_info().sms * per_sm, p.n_tiles, b.tc_max_ctas);
+  if (shape) {
+    shape->tiles = p.n_tiles;
+    shape->ctas = grid;
+  }
+  k_dense_tc<K, SPLIT, RENORM><<<grid, kTcThreads, smem, s>>>(a, (const float4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -360,10 +364,11 @@ size_t tc_b_floats(int k) { return 2u * (size_t)(2 << k) * (size_t)(2 << k); }
 
 void tc_build_b(const Block &b, float *out) { build_tc_b(b, out); }
 
-cudaError_t run_dense_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s) {
+cudaError_t run_dense_tc(float2 *a, int n, const Block &b, const void *dev_b, int *err, cudaStream_t s,
+                         LaunchShape *shape) {
   switch (b.k) {
-    case 4: return run_tc<4, true, true>(a, n, b, dev_b, err, s);
-    case 5: return run_tc<5, true, true>(a, n, b, dev_b, err, s);
+    case 4: return run_tc<4, true, true>(a, n, b, dev_b, err, s, shape);
+    case 5: return run_tc<5, true, true>(a, n, b, dev_b, err, s, shape);
     default: return cudaErrorInvalidValue;
   }
 }

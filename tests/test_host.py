@@ -46,6 +46,31 @@ def test_every_declared_symbol_is_exported():
         getattr(qs.load(), n)
 
 
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    the C compiler gives the header's structs (a mismatch would silently pass
+    wrong options or misread records)."""
+    structs = {"qs_opts": qs.qs_opts, "qs_block_record": qs.qs_block_record,
+               "qs_profile_summary": qs.qs_profile_summary, "qs_class_table": qs.qs_class_table,
+               "qs_batch_info_t": qs.qs_batch_info_t, "qs_exchange_layout": qs.qs_exchange_layout}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "qs.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", qbuild.INC, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, field, value = line.split()
+        cls = structs[name]
+        got = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
+
+
 def test_library_built_for_sm_103a():
     out = subprocess.run(["cuobjdump", "--list-elf", qs.library_path()], capture_output=True, text=True)
     if out.returncode != 0:
