@@ -133,6 +133,18 @@ typedef struct {
                            launch (normally one wave of resident CTAs, no more than there are
                            tiles), so that every CTA loops over several tiles even on a small
                            state; the block records report tiles and CTAs */
+  int n_global;         /* sharding tier (qs_plan only; 0 elsewhere): the top n_global physical
+                           bits are global -- a state sharded over 2^n_global ranks, one shard per
+                           value of those bits (Sec. II-B's file segment, across ranks). The plan
+                           then acts on global bits only diagonally (controls, phases: a shard
+                           knows its own global bits) and, before a gate that acts on a global
+                           bit non-diagonally, exchanges that bit with the local bit whose next
+                           non-diagonal use lies furthest ahead (a virtual swap of the two bits,
+                           Sec. III-D: ranks differing in the global bit swap half of their
+                           shards); records of kind 5 mark those exchanges and perm follows
+                           them. Blocks may still name global bits: their matrices are then
+                           block-diagonal in them. 0..n-2; qs_apply_circuit and batches
+                           return QS_EUNSUPPORTED for n_global > 0 (one GPU, no sharded runner) */
 } qs_opts;
 
 void qs_default_opts(qs_opts *out);
@@ -140,6 +152,9 @@ void qs_default_opts(qs_opts *out);
 typedef struct qs_state qs_state;
 
 /*
+ * Sec. II-B (full-state, Schroedinger-style simulation): the simulator keeps
+ * all 2^n complex amplitudes of an n-qubit system in memory and updates them
+ * gate by gate. This allocates that state vector in HBM.
  * Allocates a state of n qubits in library-owned device memory on the
  * current device and sets it to |0...0> with perm = identity. cuda_stream is
  * a cudaStream_t (NULL = legacy default stream) that all work on the state is
@@ -148,16 +163,20 @@ typedef struct qs_state qs_state;
 qs_status qs_alloc_state(int n, qs_dtype dtype, void *cuda_stream, qs_state **out);
 
 /*
+ * Sec. II-B: the same 2^n-amplitude state vector, in memory the caller owns.
  * Wraps caller-owned device memory (for example a torch tensor) of
  * 2^n amplitudes of the given dtype, 16-byte aligned. The contents are left
  * as they are (perm = identity); qs_free_state does not free the memory.
  */
 qs_status qs_attach_state(void *dev_ptr, int n, qs_dtype dtype, void *cuda_stream, qs_state **out);
 
-/* Releases the handle (and the amplitudes when library-owned). NULL is a no-op. */
+/* Sec. II-B: releases the state vector's handle (and the amplitudes when
+ * library-owned). NULL is a no-op. */
 void qs_free_state(qs_state *st);
 
-/* Sets the state to the logical basis state |x> and perm to identity. */
+/* Sec. II-B: sets the state to the logical basis state |x> (the state a
+ * simulation starts from) and perm to identity. Asynchronous on the state's
+ * stream. */
 qs_status qs_set_basis(qs_state *st, uint64_t x);
 
 /*
@@ -205,7 +224,9 @@ typedef struct {
   int32_t index;     /* launch order within the last apply call */
   uint8_t kind;      /* 0 dense block, 1 diagonal block, 2 physical bit exchange,
                         3 tile pass (QS_TILE: several blocks in one HBM pass),
-                        4 phase polynomial (a diagonal run wider than opts->diag_max) */
+                        4 phase polynomial (a diagonal run wider than opts->diag_max),
+                        5 exchange of a local bit (qubits[0]) with a global one (qubits[1])
+                          (qs_plan with opts->n_global > 0) */
   uint8_t k;         /* targets (dense) / table qubits (diagonal) / 2 (exchange) /
                         tile qubits (tile pass) */
   uint8_t nctrl;     /* control bits that must be 1: only 2^(n-nctrl) amplitudes move */
@@ -352,10 +373,14 @@ qs_status qs_tc_exchange_layout(int n, int k, const int *targets, uint64_t cmask
  */
 qs_status qs_fold_rotations(int n, const qs_gate *in, size_t n_in, qs_gate *out, size_t cap, size_t *n_out);
 
-/* Logical->physical map: perm_out[l] = physical bit of logical qubit l (n entries). */
+/* Sec. III-D (virtual swap): a SWAP gate is not executed but relabels qubits;
+ * this returns the resulting logical->physical map: perm_out[l] = physical
+ * bit of logical qubit l (n entries, host memory the caller owns). */
 qs_status qs_get_perm(const qs_state *st, int8_t *perm_out);
 
 /*
+ * Sec. II-B: a full-state simulation ends in the final probability
+ * distribution of the measured qubits; this is that distribution.
  * Marginal probabilities of m logical qubits (FP64 accumulation on the GPU):
  * host_out[b] = sum of |a_i|^2 over logical indices i whose bit
  * logical_qubits[j] equals bit j of b; 2^m doubles, m in 0..min(n, 26).
@@ -388,10 +413,13 @@ qs_status qs_measure_probs(qs_state *st, const int *logical_qubits, int m, doubl
 qs_status qs_probs_noalloc(const void *dev_amps, int n, qs_dtype dtype, const int *phys_bits, int m,
                            double *dev_out, void *cuda_stream);
 
-/* Squared norm sum |a_i|^2 in FP64. Synchronises the stream. */
+/* Sec. II-B: the total probability (squared norm sum |a_i|^2) of the state
+ * vector in FP64. Synchronises the stream. */
 qs_status qs_norm(qs_state *st, double *host_out);
 
 /*
+ * Sec. II-B (full-state simulation can expose the intermediate or final
+ * state) and Sec. III-D (the relabelling of virtual swap, undone on request).
  * Copies the amplitudes to host memory (2^n of the state's dtype). With
  * logical_order != 0 the state is first brought to perm = identity on the
  * GPU by physical bit exchanges (which changes the device layout and perm);
@@ -491,6 +519,7 @@ qs_status qs_batch_info(const qs_batch *b, qs_batch_info_t *out);
 void qs_batch_free(qs_batch *b);
 
 /*
+ * Sec. IV-E (many simulation runs of one circuit family, e.g. QAOA).
  * One-shot batch: qs_batch_create + one qs_batch_run + qs_batch_sync +
  * qs_batch_free with the same arguments (NULL stream: the batch's own). Each
  * state is set to |0...0> and its circuit applied in one persistent launch;

@@ -65,7 +65,8 @@ class qs_opts(ctypes.Structure):
                 ("peak_gbs", ctypes.c_double), ("tc_precision", ctypes.c_int),
                 ("test_wait_timeout", ctypes.c_int), ("tile_bits", ctypes.c_int),
                 ("tile_k", ctypes.c_int), ("fuse_lookahead", ctypes.c_int),
-                ("no_shuffles", ctypes.c_int), ("tc_exchange", ctypes.c_int), ("tc_max_ctas", ctypes.c_int)]
+                ("no_shuffles", ctypes.c_int), ("tc_exchange", ctypes.c_int), ("tc_max_ctas", ctypes.c_int),
+                ("n_global", ctypes.c_int)]
 
 
 class qs_class_table(ctypes.Structure):

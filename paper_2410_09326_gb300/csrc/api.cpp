@@ -294,6 +294,9 @@ qs_status qs_apply_circuit(qs_state *st, const qs_gate *gates, size_t n_gates, u
   qs_opts o;
   if (opts) o = *opts;
   else qs_default_opts(&o);
+  if (o.n_global != 0)
+    return fail(QS_EUNSUPPORTED, "qs_apply_circuit: global bits (opts.n_global) need a sharded runner; "
+                                 "qs_plan plans their exchanges");
   DeviceGuard dg(st->device);
   // fold the timings of an earlier profiled call that has finished
   fold_records(st, false);

@@ -291,6 +291,8 @@ qs_status qs_batch_create(qs_state *const *states, const qs_gate *const *gates, 
                           uint64_t flags, const qs_opts *opts, void *cuda_stream, qs_batch **out) {
   if (!out || !states || !gates || !n_gates || count <= 0) return bfail(QS_EINVAL, "qs_batch_create: bad arguments");
   *out = nullptr;
+  if (opts && opts->n_global != 0)
+    return bfail(QS_EUNSUPPORTED, "qs_batch_create: global bits (opts.n_global) are for qs_plan only");
   qs_batch *bt = new (std::nothrow) qs_batch();
   if (!bt) return bfail(QS_ENOMEM, "qs_batch_create: host allocation failed");
   if (opts) bt->opts = *opts;

@@ -593,6 +593,78 @@ qs_status tile_plan(int n, const std::vector<qs_gate> &pg, const std::vector<int
   return QS_OK;
 }
 
+// Fusion and classification of the physical gates pg[idx...] (one segment
+// of the circuit between global-tier exchanges); appends the blocks.
+qs_status plan_segment(int n, const std::vector<qs_gate> &pg, const std::vector<int> &all, uint64_t flags,
+                       const qs_opts &opts, int D, int K, bool c128, bool allow_phase, std::vector<Block> &plan,
+                       std::string &err) {
+  const bool fuse = flags & QS_FUSE;
+  const bool dfuse = flags & QS_DIAG;
+  std::vector<Pending> groups;
+  const bool tiled = (flags & QS_TILE) && n > tile_bits_of(opts, c128);
+  if (tiled) {
+    std::vector<Block> tplan;
+    qs_status ts = tile_plan(n, pg, all, opts, c128, tplan, err);
+    if (ts != QS_OK) return ts;
+    for (Block &b : tplan) plan.push_back(std::move(b));
+    return QS_OK;
+  }
+  if (!fuse && !dfuse) {
+    groups.resize(all.size());
+    for (size_t i = 0; i < all.size(); i++) {
+      const qs_gate &g = pg[all[i]];
+      groups[i].members.push_back(all[i]);
+      for (int j = 0; j < g.nq; j++) groups[i].qmask |= 1ull << g.q[j];
+      groups[i].all_diag = op_info(g.op).diagonal;
+    }
+  } else {
+    // diagonal runs: up to D qubits as a phase table, any width as a phase
+    // polynomial (states of at least 11 qubits, which the kernel needs)
+    const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
+    const int dlimit = phase_ok ? 64 : D;
+    auto limit = [&](bool nd) { return nd ? (dfuse ? dlimit : std::max(K, 1)) : K; };
+    if (opts.fuse_lookahead > 0) {
+      // the roll-out heuristic usually saves blocks but is not guaranteed
+      // to, and its best horizon and tie-break vary: plain first fit and
+      // roll-outs of L, 4L/3 and 5L/3 gates (ties broken by the width of the
+      // last 6 or 12 blocks) run side by side on host threads, and the
+      // grouping with the fewest blocks is launched (earliest on a tie)
+      constexpr int kVariants = 6;
+      std::vector<Pending> alt[kVariants];
+      const int L = opts.fuse_lookahead;
+      const int horizons[kVariants] = {0, L, L, L + L / 3, L + L / 3, L + 2 * L / 3};
+      const int tails[kVariants] = {0, 6, 12, 6, 12, 6};
+      run_tasks(kVariants, [&](size_t v) {
+        if (v == 0)
+          greedy_groups(pg, all, alt[0], [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
+            return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
+          });
+        else
+          lookahead_groups(pg, all, alt[v], limit, horizons[v], tails[v]);
+      });
+      int best = 0;
+      for (int v = 1; v < kVariants; v++)
+        if (alt[v].size() < alt[best].size()) best = v;
+      groups.swap(alt[best]);
+    } else {
+      greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
+        return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
+      });
+    }
+  }
+
+  // (3) products and classification
+  std::vector<Block> done(groups.size());
+  std::vector<char> keep(groups.size(), 0);
+  const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
+  parallel_for(groups.size(), [&](size_t i) {
+    if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i], D, phase_ok) ? 1 : 0;
+  });
+  for (size_t i = 0; i < groups.size(); i++)
+    if (keep[i]) plan.push_back(std::move(done[i]));
+  return QS_OK;
+}
+
 }  // namespace
 
 void parallel_blocks(size_t n, const std::function<void(size_t)> &f) { parallel_for(n, f); }
@@ -626,7 +698,7 @@ void fill_record(const Block &b, int index, int n, int amp_bytes, qs_block_recor
 
 double block_bytes(const Block &b, int n, int amp_bytes) {
   double amps = std::ldexp(1.0, n - b.nctrl);
-  if (b.kind == BK_PERMUTE) amps = std::ldexp(1.0, n - 1);
+  if (b.kind == BK_PERMUTE || b.kind == BK_GLOBAL) amps = std::ldexp(1.0, n - 1);
   return 2.0 * amps * amp_bytes;
 }
 
@@ -666,7 +738,6 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   }
   const bool vswap = flags & QS_VSWAP;
   const bool fuse = flags & QS_FUSE;
-  const bool dfuse = flags & QS_DIAG;
   int K = fuse ? QS_FUSE_K_OF(flags) : 0;
   if (fuse && K == 0) K = 4;
   if (K > QS_MAX_FUSE) {
@@ -680,6 +751,10 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
   }
   if (opts.tc_max_ctas < 0) {
     err = "opts.tc_max_ctas must not be negative";
+    return QS_EINVAL;
+  }
+  if (opts.n_global < 0 || opts.n_global > n - 1 || (opts.n_global > 0 && n - opts.n_global < 2)) {
+    err = "opts.n_global out of range (0..n-2 global bits, two local bits at least)";
     return QS_EINVAL;
   }
   if (flags & QS_TILE) {
@@ -745,7 +820,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
       for (int lowq = 0; lowq < 2; lowq++) {
         if (heat[lowq] == 0) continue;
         int best = -1;
-        for (int q = n - 1; q >= 5; q--) {
+        for (int q = n - 1 - opts.n_global; q >= 5; q--) {
           if (std::find(used.begin(), used.end(), q) != used.end()) continue;
           if (best < 0 || heat[q] < heat[best]) best = q;
         }
@@ -769,74 +844,81 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     }
   }
 
-  // (2) grouping
-  std::vector<Pending> groups;
-  std::vector<int> all(pg.size());
-  for (size_t i = 0; i < pg.size(); i++) all[i] = (int)i;
-  const bool tiled = (flags & QS_TILE) && n > tile_bits_of(opts, c128);
-  if (tiled) {
-    std::vector<Block> tplan;
-    qs_status ts = tile_plan(n, pg, all, opts, c128, tplan, err);
-    if (ts != QS_OK) return ts;
-    plan.reserve(tplan.size() + reloc.size());
-    push_exchanges(reloc, plan);
-    for (Block &b : tplan) plan.push_back(std::move(b));
-    return QS_OK;
-  }
-  if (!fuse && !dfuse) {
-    groups.resize(pg.size());
+  // (1c) global tier: the top n_global physical bits are held by other
+  // ranks (one shard per value of those bits). A gate acting non-diagonally
+  // on a global bit first needs that bit exchanged with a local one (a
+  // virtual swap of the two bits: a pairwise half-shard exchange between the
+  // ranks that differ in the global bit); the plan records the exchange and
+  // every later gate, and perm, follow the relabelling. The local bit taken
+  // is the one whose next non-diagonal use lies furthest ahead (never used
+  // again first; ties: the highest bit), so that exchanges stay rare. Gates
+  // that are diagonal on a global bit (controls, phases) need no exchange: a
+  // shard knows its global bits.
+  std::vector<size_t> cuts;                   // segment starts in pg
+  std::vector<std::pair<int, int>> gswaps;    // (local, global) exchanged at each cut
+  const int nloc = n - opts.n_global;
+  if (opts.n_global > 0) {
+    auto next_use = [&](size_t from, int q) {
+      for (size_t i = from; i < pg.size(); i++)
+        for (int j = 0; j < pg[i].nq; j++)
+          if (pg[i].q[j] == q && !gate_diag_on(pg[i], j)) return i;
+      return pg.size();
+    };
     for (size_t i = 0; i < pg.size(); i++) {
-      groups[i].members.push_back((int)i);
-      for (int j = 0; j < pg[i].nq; j++) groups[i].qmask |= 1ull << pg[i].q[j];
-      groups[i].all_diag = op_info(pg[i].op).diagonal;
-    }
-  } else {
-    // diagonal runs: up to D qubits as a phase table, any width as a phase
-    // polynomial (states of at least 11 qubits, which the kernel needs)
-    const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
-    const int dlimit = phase_ok ? 64 : D;
-    auto limit = [&](bool nd) { return nd ? (dfuse ? dlimit : std::max(K, 1)) : K; };
-    if (opts.fuse_lookahead > 0) {
-      // the roll-out heuristic usually saves blocks but is not guaranteed
-      // to, and its best horizon and tie-break vary: plain first fit and
-      // roll-outs of L, 4L/3 and 5L/3 gates (ties broken by the width of the
-      // last 6 or 12 blocks) run side by side on host threads, and the
-      // grouping with the fewest blocks is launched (earliest on a tie)
-      constexpr int kVariants = 6;
-      std::vector<Pending> alt[kVariants];
-      const int L = opts.fuse_lookahead;
-      const int horizons[kVariants] = {0, L, L, L + L / 3, L + L / 3, L + 2 * L / 3};
-      const int tails[kVariants] = {0, 6, 12, 6, 12, 6};
-      run_tasks(kVariants, [&](size_t v) {
-        if (v == 0)
-          greedy_groups(pg, all, alt[0], [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
-            return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
-          });
-        else
-          lookahead_groups(pg, all, alt[v], limit, horizons[v], tails[v]);
-      });
-      int best = 0;
-      for (int v = 1; v < kVariants; v++)
-        if (alt[v].size() < alt[best].size()) best = v;
-      groups.swap(alt[best]);
-    } else {
-      greedy_groups(pg, all, groups, [&](const Pending &p, int, uint64_t gmask, uint64_t, bool gdiag) {
-        return popcount64(p.qmask | gmask) <= limit(p.all_diag && gdiag);
-      });
+      for (int j = 0; j < pg[i].nq; j++) {
+        const int G = pg[i].q[j];
+        if (G < nloc || gate_diag_on(pg[i], j)) continue;
+        int L = -1;
+        size_t far = 0;
+        for (int q = nloc - 1; q >= 0; q--) {
+          bool in_gate = false;
+          for (int jj = 0; jj < pg[i].nq; jj++) in_gate |= pg[i].q[jj] == q;
+          if (in_gate) continue;
+          const size_t u = next_use(i, q);
+          if (L < 0 || u > far) {
+            L = q;
+            far = u;
+          }
+        }
+        if (L < 0) {
+          err = "global tier: no local bit free for an exchange";
+          return QS_EUNSUPPORTED;
+        }
+        for (size_t k2 = i; k2 < pg.size(); k2++)
+          for (int jj = 0; jj < pg[k2].nq; jj++) {
+            if (pg[k2].q[jj] == G) pg[k2].q[jj] = (uint8_t)L;
+            else if (pg[k2].q[jj] == L) pg[k2].q[jj] = (uint8_t)G;
+          }
+        for (int l = 0; l < n; l++) {
+          if (perm[l] == G) perm[l] = (int8_t)L;
+          else if (perm[l] == L) perm[l] = (int8_t)G;
+        }
+        cuts.push_back(i);
+        gswaps.push_back({L, G});
+      }
     }
   }
 
-  // (3) products and classification
-  std::vector<Block> done(groups.size());
-  std::vector<char> keep(groups.size(), 0);
-  const bool phase_ok = dfuse && allow_phase && n > QS_MAX_DIAG;
-  parallel_for(groups.size(), [&](size_t i) {
-    if (!groups[i].members.empty()) keep[i] = finish_block(pg, groups[i], true, done[i], D, phase_ok) ? 1 : 0;
-  });
-  plan.reserve(groups.size() + reloc.size());
   push_exchanges(reloc, plan);
-  for (size_t i = 0; i < groups.size(); i++)
-    if (keep[i]) plan.push_back(std::move(done[i]));
+  size_t seg_begin = 0;
+  for (size_t sgi = 0; sgi <= cuts.size(); sgi++) {
+    const size_t seg_end = sgi < cuts.size() ? cuts[sgi] : pg.size();
+    std::vector<int> idx;
+    for (size_t i = seg_begin; i < seg_end; i++) idx.push_back((int)i);
+    qs_status st = plan_segment(n, pg, idx, flags, opts, D, K, c128, allow_phase, plan, err);
+    if (st != QS_OK) return st;
+    if (sgi < cuts.size()) {
+      Block b;
+      b.kind = BK_GLOBAL;
+      b.k = 2;
+      b.q[0] = gswaps[sgi].first;
+      b.q[1] = gswaps[sgi].second;
+      b.n_gates = 0;
+      b.meta = 3;
+      plan.push_back(std::move(b));
+    }
+    seg_begin = seg_end;
+  }
   const bool tf32 = opts.tc_precision == 1;
   for (Block &b : plan) {
     b.tc = (flags & QS_TC) && b.kind == BK_DENSE && b.k >= 4 && b.k <= (tf32 ? 5 : 6);

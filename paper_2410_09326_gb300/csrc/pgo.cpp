@@ -24,6 +24,8 @@ int block_class(const Block &b) {
   // phase polynomials share the diagonal kind with the "low" bit set, which
   // only dense classes use otherwise
   if (b.kind == BK_PHASE) return 64 + 8 * BK_DIAG + 7;
+  // global-bit exchanges (planning only) likewise take an unused "low" class
+  if (b.kind == BK_GLOBAL) return 64 + 8 * BK_PERMUTE + 2;
   // "low": bits 0 and 1 are both targets, so a thread's group is a run of
   // >= 4 contiguous amplitudes and a warp's accesses are strided
   int low = 0;

@@ -41,7 +41,9 @@ bool gate_diag_on(const qs_gate &g, int j);
 // ---------------------------------------------------------------------------
 // Plan: the list of kernels one qs_apply_circuit call launches
 // ---------------------------------------------------------------------------
-enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2, BK_TILE = 3, BK_PHASE = 4 };
+// BK_GLOBAL: an exchange of a local with a global physical bit (opts.n_global
+// > 0, qs_plan only): q[0] the local bit, q[1] the global one.
+enum BlockKind : uint8_t { BK_DENSE = 0, BK_DIAG = 1, BK_PERMUTE = 2, BK_TILE = 3, BK_PHASE = 4, BK_GLOBAL = 5 };
 
 constexpr int kMaxFixed = 24;  // targets + controls handled by the index insert
 constexpr int kMaxTileBits = 14;  // widest shared-memory tile (QS_TILE)

@@ -311,10 +311,23 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
 // target equals h: warp w and warp w + 4 load the same 32 groups' two halves,
 // each exactly as a 5-target exchange warp (the highest target fixed per
 // half; slot bit 5 = the highest target). The row's scale and norms are
-// combined over the two halves through shared memory. The 6-target operands
-// (A and B, hi and lo: 128 KB) fill an SM with one CTA; the next tile is
-// gathered into registers while the current tile's MMAs run and its results
-// are stored.
+// combined over the two halves through shared memory.
+//
+// Operand placement. A 6-target tile's A (hi and lo, 64 KB) and B (64 KB)
+// would fill shared memory and leave no room to stage loads, so A lives in
+// tensor memory instead: the MMA reads its A operand from TMEM (lane m = row
+// m, K packed two FP16 values per 32-bit column, 8 columns per K step of
+// 16), written by the converting threads with tcgen05.st (thread (h, r)
+// writes lane r, columns [32 h, 32 h + 32) of each half). TMEM columns:
+// [0, 128) large products, [128, 256) small products, then two A buffers of
+// 128 columns (hi, lo). Shared memory holds B and two 64 KB staging areas.
+//
+// Pipeline per tile i (one CTA per SM): while the MMAs of tile i run, the
+// CTA converts tile i + 1 (read back from its staging area, which is then
+// refilled with tile i + 3 by cp.async) into the other A buffer; then it
+// waits for tile i's MMAs, reads the products, rescales, exchanges back and
+// stores, and issues tile i + 1's MMAs. Two tiles (128 KB) are in flight per
+// SM at all times, and no registers hold them.
 __global__ void __launch_bounds__(2 * kTcThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
@@ -322,17 +335,17 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   constexpr int NV = 16;        // 16-byte registers per thread (32 amplitudes)
   constexpr int RB = 4;         // register bits
   constexpr int KR = 128;       // real K = N
-  constexpr uint32_t A_BYTES = 128u * KR * 2u;     // one of hi / lo
   constexpr uint32_t B_BYTES = (uint32_t)KR * KR * 2u;
+  constexpr uint32_t STAGE_BYTES = (uint32_t)NV * NT * 16u;  // one tile
   constexpr uint32_t SBO = (KR / 8) * 128u;
   constexpr uint32_t LBO = 128u;
-  constexpr uint32_t NCOLS = 256;                  // large + small products
+  constexpr uint32_t NCOLS = 512;
+  constexpr uint32_t COL_A = 256;                  // A buffer u: hi at COL_A + 128 u, lo 64 after
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *sA_hi = smem;
-  unsigned char *sA_lo = smem + A_BYTES;
-  unsigned char *sB = smem + 2 * A_BYTES;  // hi then lo
+  unsigned char *sB = smem;                   // hi then lo
+  unsigned char *sStage = smem + 2 * B_BYTES; // two staging areas
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ float red_in[2 * NT];
@@ -341,7 +354,6 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const int r = tid & 127;
   const int h = tid >> 7;
   for (int i = tid; i < (int)(2 * B_BYTES / 16); i += NT) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
   if (warp == 0) {
@@ -353,14 +365,15 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  // B was written by ordinary stores: make it visible to the tensor cores
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   const uint32_t mbar_a = smem_addr(&mbar);
-  const uint32_t a_hi = smem_addr(sA_hi), a_lo = smem_addr(sA_lo);
   const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
-  const uint32_t row_off = (uint32_t)(r >> 3) * SBO + (uint32_t)(r & 7) * 16u;
+  // this thread's TMEM lane (row r of A and D) in column 0
   const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 
   uint64_t lane_off = h ? (1ull << p.th) : 0ull;
@@ -377,24 +390,36 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       if ((rr >> j) & 1) o += roff[j];
     return o;
   };
+  auto tile_base = [&](long long t) {
+    return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
+  };
   const LaneExchange xch(p, lane);
 
-  float4 v[NV];
-  uint64_t base = 0;
-  auto gather = [&](long long t) {
-    const bool ok = t < p.n_tiles;  // uniform over the CTA
-    base = ok ? (insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask) : 0;
+  // tile t into staging area u: this thread's 16 chunks, one commit group per
+  // tile (empty past the last tile, so the group count stays uniform)
+  auto stage_in = [&](long long t, int u) {
+    if (t < p.n_tiles) {
+      const uint64_t b = tile_base(t);
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
 #pragma unroll
-    for (int q = 0; q < NV; q++)
-      v[q] = ok ? *reinterpret_cast<const float4 *>(a + base + offset(q)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + b + offset(q));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   };
-
-  uint32_t phase = 0;
-  bool aborted = false;
-  long long tile = blockIdx.x;
-  gather(tile);
-  for (; tile < p.n_tiles; tile += gridDim.x) {
+  // tile t (staged in area u) -> A buffer u: exchange, row scale, FP16
+  // hi/lo split, tcgen05.st; refills area u with tile t + 2 G; returns the
+  // row's input norm (both halves)
+  const long long G = gridDim.x;
+  auto convert = [&](long long t, int u) -> float {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    float4 v[NV];
+    const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+    for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
     xch.run<NV>(v);
+    // the shuffles consumed the values read back: refill this thread's own
+    // chunks of the area with tile t + 2 G
+    stage_in(t + 2 * G, u);
     float mx = 0.f, nin = 0.f;
 #pragma unroll
     for (int q = 0; q < NV; q++) {
@@ -409,37 +434,64 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
     const float sc = ldexpf(1.f, -e);
+    // slot 2 q + c (register q, element c) holds K = 64 h + 4 q + 2 c (re) and
+    // + 1 (im): column 32 h + 2 q + c of its half
+    uint32_t hi[32], lo[32];
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-      const float x[8] = {v[2 * c].x * sc,     v[2 * c].y * sc,     v[2 * c].z * sc,     v[2 * c].w * sc,
-                          v[2 * c + 1].x * sc, v[2 * c + 1].y * sc, v[2 * c + 1].z * sc, v[2 * c + 1].w * sc};
-      uint4 hi, lo;
-      split_row(x, hi, lo);
-      *reinterpret_cast<uint4 *>(sA_hi + row_off + (8 * h + c) * LBO) = hi;
-      *reinterpret_cast<uint4 *>(sA_lo + row_off + (8 * h + c) * LBO) = lo;
+    for (int q = 0; q < NV; q++) {
+      const float x[4] = {v[q].x * sc, v[q].y * sc, v[q].z * sc, v[q].w * sc};
+#pragma unroll
+      for (int c = 0; c < 2; c++) {
+        const __half2 hh = __floats2half2_rn(x[2 * c], x[2 * c + 1]);
+        const float2 hf = __half22float2(hh);
+        hi[2 * q + c] = *reinterpret_cast<const uint32_t *>(&hh);
+        lo[2 * q + c] = pack_half2(x[2 * c] - hf.x, x[2 * c + 1] - hf.y);
+      }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t acol = lane_base + COL_A + 128u * (uint32_t)u + 32u * (uint32_t)h;
+    TmemSt<32>::run(acol, hi);
+    TmemSt<32>::run(acol + 64, lo);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    return nin;
+  };
+  // the MMAs of the tile in A buffer u (one thread): D = A B^T, large and
+  // small products in their own columns; completion on the mbarrier
+  auto issue = [&](int u) {
     if (tid == 0) {
+      const uint32_t a_hi = tmem + COL_A + 128u * (uint32_t)u, a_lo = a_hi + 64u;
 #pragma unroll
       for (int ks = 0; ks < KR / 16; ks++) {
         const uint32_t koff = (uint32_t)ks * 2u * LBO;
-        const uint64_t dah = make_desc(a_hi + koff, LBO, SBO);
-        const uint64_t dal = make_desc(a_lo + koff, LBO, SBO);
         const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
         const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
         const uint32_t acc = ks > 0 ? 1u : 0u;
-        mma_f16(tmem, dah, dbh, IDESC, acc);
-        mma_f16(tmem + KR, dah, dbl, IDESC, acc);
-        mma_f16(tmem + KR, dal, dbh, IDESC, 1u);
+        mma_f16_ta(tmem, a_hi + 8u * ks, dbh, IDESC, acc);
+        mma_f16_ta(tmem + KR, a_hi + 8u * ks, dbl, IDESC, acc);
+        mma_f16_ta(tmem + KR, a_lo + 8u * ks, dbh, IDESC, 1u);
       }
       if (!p.withhold_commit) mma_commit(mbar_a);
     }
-    const uint64_t cur_base = base;
-    const float cur_nin = nin;
-    gather(tile + gridDim.x);  // next tile, in flight during the MMAs and the stores
+  };
+  auto publish = [&]() {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+  };
+
+  uint32_t phase = 0;
+  bool aborted = false;
+  long long tile = blockIdx.x;
+  stage_in(tile, 0);
+  stage_in(tile + G, 1);
+  float nin_cur = 0.f, nin_next = 0.f;
+  if (tile < p.n_tiles) nin_cur = convert(tile, 0);
+  publish();
+  if (tile < p.n_tiles) issue(0);
+  for (int it = 0; tile < p.n_tiles; tile += G, it++) {
+    const int u = it & 1;
+    // the next tile into the other A buffer while this tile's MMAs run
+    const bool more = tile + G < p.n_tiles;  // uniform over the CTA
+    if (more) nin_next = convert(tile + G, u ^ 1);
     const bool ok = mbar_wait(mbar_a, phase);
     phase ^= 1;
     if (!__syncthreads_and(ok)) {
@@ -448,7 +500,7 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t cb = lane_base + 64u * h;
+    const uint32_t cb = lane_base + 64u * (uint32_t)h;
     float nout = 0.f;
 #pragma unroll
     for (int hh = 0; hh < 4; hh++) {
@@ -465,7 +517,8 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
     red_out[tid] = nout;
     __syncthreads();
     nout += red_out[tid ^ kTcThreads];
-    const float f = nout > 0.f ? sqrtf(cur_nin / nout) : 1.f;
+    const float f = nout > 0.f ? sqrtf(nin_cur / nout) : 1.f;
+    const uint64_t cur_base = tile_base(tile);
 #pragma unroll
     for (int hh = 0; hh < 4; hh++) {
       uint32_t rb[16], rs[16];
@@ -483,7 +536,12 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
 #pragma unroll
       for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
     }
+    // every thread has read the products and written the next A buffer
+    publish();
+    if (more) issue(u ^ 1);
+    nin_cur = nin_next;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (aborted) {
@@ -544,8 +602,8 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
                        cudaStream_t s, LaunchShape *shape) {
   TcXParam p;
   fill_xparam(6, n, b, x, p);
-  // A (hi + lo) of 64 KB, B (hi + lo) of 64 KB
-  const size_t smem = 2 * (size_t)128 * 128 * 2 + 2 * (size_t)128 * 128 * 2;
+  // B (hi + lo) of 64 KB, two 64 KB staging areas (A lives in TMEM)
+  const size_t smem = 2 * (size_t)128 * 128 * 2 + 2 * (size_t)16 * 2 * kTcThreads * 16;
   static thread_local int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);

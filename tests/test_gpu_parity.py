@@ -521,6 +521,21 @@ def test_bounded_wait_times_out_and_state_recovers(k, exchange):
         qs.qs_free_state(st)
 
 
+def test_apply_rejects_global_bits():
+    """The global-bit tier (opts.n_global) is planned by qs_plan only: a
+    single-GPU apply call refuses it before launching anything."""
+    st = qs.qs_alloc_state(10, qs.QS_C64)
+    try:
+        o = qs.qs_default_opts()
+        o.n_global = 1
+        with pytest.raises(qs.QsError) as e:
+            qs.qs_apply_circuit(st, qs.gates_to_array([("h", [9])]), qs.QS_PLAIN, o)
+        assert e.value.status == qs.QS_EUNSUPPORTED
+        assert qs.qs_measure_probs(st, [9])[0] == 1.0
+    finally:
+        qs.qs_free_state(st)
+
+
 def test_chrome_trace_of_a_profiled_call(tmp_path):
     """A profiled apply call (QS_PROFILE) exported as a Chrome trace: one
     event per launched block, durations summing to the profile's device time,

@@ -5,15 +5,18 @@ process that reserved its HBM up front through its own pool, or one that
 must not risk the synchronisation cudaMalloc/cudaFree may imply). Its
 scratch is a fixed array inside the library, so the test checks, through the
 C ABI, that two calls in a row give the same marginals as qs_measure_probs
-(which uses state-owned scratch), within the tolerances of the other
-probability tests. The file sorts last so that a failure here comes after
-every other test has run; it also passes on its own in a fresh process.
+(which uses state-owned scratch) and as the FP64 oracle, within the
+tolerances of the other probability tests, and that the library's count of
+live device bytes does not move across the calls. The file sorts last so
+that a failure here comes after every other test has run; it also passes on
+its own in a fresh process.
 """
 
 import numpy as np
 import pytest
 
 import circuitgen as cg
+import oracle
 import paper_2410_09326_gb300 as qs
 
 pytestmark = pytest.mark.gpu
@@ -36,12 +39,42 @@ def test_noalloc_matches_measure_probs_twice(dtype, tol):
         for logical in ([], [0], [3, 17], list(range(12)), [21, 5, 9, 0, 14]):
             want = qs.qs_measure_probs(st, logical)
             phys = [int(perm[l]) for l in logical]
+            out = torch.full((1 << len(logical),), -1.0, dtype=torch.float64, device="cuda")
+            live = qs.qs_memory_in_use()
             for _ in range(2):  # the shared array keeps the previous call's contents
-                out = torch.full((1 << len(logical),), -1.0, dtype=torch.float64, device="cuda")
+                out.fill_(-1.0)
                 qs.qs_probs_noalloc(amps, n, dtype, phys, out.data_ptr(), stream=stream)
                 stream.synchronize()
                 got = out.cpu().numpy()
                 assert np.abs(got - want).max() < tol, (logical, np.abs(got - want).max())
+            assert qs.qs_memory_in_use() == live
+    finally:
+        qs.qs_free_state(st)
+
+
+@pytest.mark.parametrize("dtype,tol", [(qs.QS_C64, 1e-6), (qs.QS_C128, 1e-13)])
+def test_noalloc_matches_the_oracle(dtype, tol):
+    """Marginals of a 14-qubit layered circuit with SWAPs against the FP64
+    oracle's, twice in a row, the measured bits mapped through perm."""
+    torch = pytest.importorskip("torch")
+    qs.load(build_if_missing=True)
+    n = 14
+    gates = cg.random_layered(n, 6, cg.SplitMix64(654), n_swaps=5)
+    want_state, _ = oracle.simulate(cg.to_qasm(n, gates))
+    st = qs.qs_alloc_state(n, dtype)
+    try:
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(4) | qs.QS_DIAG)
+        perm = qs.qs_get_perm(st, n)
+        amps = qs.qs_device_ptr(st)
+        torch.cuda.synchronize()
+        for logical in ([13], [2, 11, 7], list(range(12)), list(range(13, 1, -1))):
+            want = oracle.probs(want_state, logical)
+            out = torch.full((1 << len(logical),), -1.0, dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                out.fill_(-1.0)
+                qs.qs_probs_noalloc(amps, n, dtype, [int(perm[l]) for l in logical], out.data_ptr())
+                torch.cuda.synchronize()
+                assert np.abs(out.cpu().numpy() - want).max() < tol, logical
     finally:
         qs.qs_free_state(st)
 
