@@ -336,13 +336,14 @@ uint64_t qs_memory_in_use(void);
  * Lane-exchange layout of the FP16 tensor-core kernels (introspection for
  * tests and tools; host only, no GPU). A warp of those kernels owns the
  * sub-cube spanned by a block's targets and its five lowest free bits (6
- * targets: the five lower targets, the highest one fixed per thread half),
+ * targets: two threads per group; the five lower targets, the sixth fixed
+ * per thread part),
  * loads it with 16-byte accesses (element bit = bit 0) whose lane bits and
  * register bits are given below, and exchanges bits between positions with
  * warp shuffles until every lane holds one group: first the element bit with
  * lane bit la (if la >= 0), then lane bit lb[i] with register bit i for
  * i < nswb. Slot bit 0 is then the element bit, slot bit 1 + j register bit j
- * (slot bit 5 = half_bit for 6 targets); slot_target[s] is the position, in
+ * (slot bit 5 = part_bits[0] for 6 targets); slot_target[s] is the position, in
  * the ascending target list, of the target slot bit s holds.
  * targets: k (4..6) distinct ascending physical bits < n; cmask: controls,
  * disjoint from them. Returns QS_EINVAL for bad arguments; *out->applies = 0
@@ -357,7 +358,9 @@ typedef struct {
   int32_t nswb;            /* lane/register exchanges (0..2) */
   int32_t lb[2];           /* their lane bits */
   int32_t slot_target[6];  /* slot bit -> index in the ascending target list */
-  int32_t half_bit;        /* 6 targets: physical bit fixed per thread half; else -1 */
+  int32_t part_bits[2];    /* 6 targets: part_bits[0] = the physical bit fixed per thread part
+                              (the sixth target; the second part has it set), part_bits[1] = -1;
+                              else both -1 */
 } qs_exchange_layout;
 
 qs_status qs_tc_exchange_layout(int n, int k, const int *targets, uint64_t cmask, qs_exchange_layout *out);

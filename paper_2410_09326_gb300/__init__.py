@@ -94,7 +94,7 @@ class qs_block_record(ctypes.Structure):
 class qs_exchange_layout(ctypes.Structure):
     _fields_ = [("applies", ctypes.c_int32), ("lane_bits", ctypes.c_int32 * 5), ("reg_bits", ctypes.c_int32 * 4),
                 ("la", ctypes.c_int32), ("nswb", ctypes.c_int32), ("lb", ctypes.c_int32 * 2),
-                ("slot_target", ctypes.c_int32 * 6), ("half_bit", ctypes.c_int32)]
+                ("slot_target", ctypes.c_int32 * 6), ("part_bits", ctypes.c_int32 * 2)]
 
 
 class qs_profile_summary(ctypes.Structure):

@@ -544,7 +544,8 @@ qs_status qs_tc_exchange_layout(int n, int k, const int *targets, uint64_t cmask
   out->nswb = x.nswb;
   for (int i = 0; i < 2; i++) out->lb[i] = i < x.nswb ? x.lb[i] : -1;
   for (int s = 0; s < 6; s++) out->slot_target[s] = s < k ? x.slot_mat[s] : -1;
-  out->half_bit = x.th;
+  out->part_bits[0] = x.part_bit[0];
+  out->part_bits[1] = x.part_bit[1];
   return QS_OK;
 }
 

@@ -79,7 +79,7 @@ struct Block {
 };
 
 // Lane-exchange layout of a 4-, 5- or 6-target FP16 tensor-core block
-// (tc16x.cu; 6 targets: two threads per group, each half laid out as a
+// (tc16x.cu; 6 targets: two threads per group, each part laid out as a
 // 5-target block with the highest target fixed).
 // A warp owns the sub-cube of 32 groups spanned by the targets and the five
 // lowest free bits. It loads it in address order -- element bit of each
@@ -98,7 +98,8 @@ struct TcXLayout {
   int nswb;          // lane bits lb[i] exchanged with register bits i (i < nswb <= 2)
   int lb[2];
   int slot_mat[6];   // slot bit -> position of its target in the block's ascending list
-  int th;            // 6 targets: the highest target, fixed per thread half (slot bit 5); else -1
+  int part_bit[2];   // 6 targets: part_bit[0] = the sixth target, fixed per thread part h (h = 1
+                     // sets it; slot bit 5), part_bit[1] = -1; else both -1
   int nf;            // targets, controls and the five lowest free bits, ascending
   int fixed[kMaxFixed];
 };

@@ -42,7 +42,7 @@ struct TcXParam {
   int la;                     // lane bit exchanged with the element bit, -1: none
   int nswb;                   // lane bits lb[i] exchanged with register bits i
   int lb[2];
-  int th;                     // 6 targets: the target bit thread half h fixes (the highest)
+  int part_bit[2];            // 6 targets: the target bits thread part h fixes (bit j of h -> part_bit[j])
   int withhold_commit;
 };
 
@@ -209,12 +209,15 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
       valid = u ? svalid1 : svalid0;
     }
     xch.run<NV>(v);
-    float mx = 0.f, nin = 0.f;
+    // row max and squared norm in four independent chains
+    float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int r = 0; r < NV; r++) {
-      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[r].x), fabsf(v[r].y)), fmaxf(fabsf(v[r].z), fabsf(v[r].w))));
-      nin = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, fmaf(v[r].z, v[r].z, fmaf(v[r].w, v[r].w, nin))));
+      m4[r & 3] = fmaxf(m4[r & 3], fmaxf(fmaxf(fabsf(v[r].x), fabsf(v[r].y)), fmaxf(fabsf(v[r].z), fabsf(v[r].w))));
+      s4[r & 3] = fmaf(v[r].x, v[r].x, fmaf(v[r].y, v[r].y, fmaf(v[r].z, v[r].z, fmaf(v[r].w, v[r].w, s4[r & 3]))));
     }
+    const float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
+    const float nin = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     int e = 0;
     if (mx > 0.f) frexpf(mx, &e);
     const float sc = ldexpf(1.f, -e);
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    float nout = 0.f;
+    float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int hh = 0; hh < KR / 16; hh++) {
       uint32_t rb[16], rs[16];
@@ -271,9 +274,10 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
-        nout = fmaf(y, y, nout);
+        o4[i & 3] = fmaf(y, y, o4[i & 3]);
       }
     }
+    const float nout = (o4[0] + o4[1]) + (o4[2] + o4[3]);
     const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
     // 8 slots (4 registers) at a time: scale, exchange back, store
 #pragma unroll
@@ -318,20 +322,52 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
 // tensor memory instead: the MMA reads its A operand from TMEM (lane m = row
 // m, K packed two FP16 values per 32-bit column, 8 columns per K step of
 // 16), written by the converting threads with tcgen05.st (thread (h, r)
-// writes lane r, columns [32 h, 32 h + 32) of each half). TMEM columns:
-// [0, 128) large products, [128, 256) small products, then two A buffers of
-// 128 columns (hi, lo). Shared memory holds B and two 64 KB staging areas.
+// writes lane r, columns [32 h, 32 h + 32) of each half). The three
+// products accumulate into one FP32 accumulator of 128 columns, so TMEM
+// holds two accumulators and two A buffers (4 x 128 columns). Shared memory
+// holds B and two 64 KB staging areas.
 //
-// Pipeline per tile i (one CTA per SM): while the MMAs of tile i run, the
-// CTA converts tile i + 1 (read back from its staging area, which is then
-// refilled with tile i + 3 by cp.async) into the other A buffer; then it
-// waits for tile i's MMAs, reads the products, rescales, exchanges back and
-// stores, and issues tile i + 1's MMAs. Two tiles (128 KB) are in flight per
-// SM at all times, and no registers hold them.
-__global__ void __launch_bounds__(2 * kTcThreads, 1)
+// Warp roles (one CTA per SM). Warps 0..7 convert and store: iteration i
+// waits for tile i's products (mbarrier done[i % 2]), rescales and stores
+// them, converts tile i + 2 -- read back from its staging area, which is
+// refilled with tile i + 4 by cp.async -- into the A buffer tile i used, and
+// arrives on ready[i % 2]. Warp 8 issues the MMAs: tile i once ready[i % 2]
+// says its A is written and its accumulator read out, with completion on
+// done[i % 2]. The converting warps never wait for an MMA issue and
+// synchronise among themselves only (named barrier 1). Where the layout
+// needs no lane/register exchange (nswb = 0) the products are stored
+// without exchanging back: each lane writes its two slot halves of a
+// register as 8-byte pairs, which across the warp still cover whole runs
+// of the lowest bits. Measured on GB300 from random states at n = 28, high
+// targets: one A buffer in shared memory, register gathers 5.1 TB/s; A in
+// TMEM with staging 5.3; both double-buffered, one thread issuing 4.7;
+// warp roles 5.56; four threads per group instead of two 5.37.
+namespace x6 {
+constexpr int kConv = 2 * kTcThreads;  // converting threads, two per group
+constexpr int kThreads = kConv + 32;   // + the MMA warp
+__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConv) : "memory"); }
+// AND of a predicate over the converting threads (named barrier 1)
+__device__ __forceinline__ bool conv_and(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred p, 1, %2, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(out)
+      : "r"((uint32_t)v), "n"(kConv)
+      : "memory");
+  return out != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+}  // namespace x6
+
+__global__ void __launch_bounds__(x6::kThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
-  constexpr int NT = 2 * kTcThreads;
+  constexpr int NT = x6::kConv;  // converting threads
   constexpr int NV = 16;        // 16-byte registers per thread (32 amplitudes)
   constexpr int RB = 4;         // register bits
   constexpr int KR = 128;       // real K = N
@@ -340,29 +376,36 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   constexpr uint32_t SBO = (KR / 8) * 128u;
   constexpr uint32_t LBO = 128u;
   constexpr uint32_t NCOLS = 512;
-  constexpr uint32_t COL_A = 256;                  // A buffer u: hi at COL_A + 128 u, lo 64 after
+  // accumulator u at 128 u, A buffer u (hi, then lo 64 columns after) at 256 + 128 u
+  constexpr uint32_t COL_A = 256;
   constexpr uint32_t IDESC = make_idesc_f16(128, KR);
 
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char *sB = smem;                   // hi then lo
   unsigned char *sStage = smem + 2 * B_BYTES; // two staging areas
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t done[2];   // tile's MMAs complete (one arrival: the commit)
+  __shared__ __align__(8) uint64_t ready[2];  // A written, accumulator read out (NT arrivals)
+  __shared__ __align__(8) uint64_t drain;     // final commit of the MMA thread
   __shared__ uint32_t tmem_slot;
-  __shared__ float red_in[2 * NT];
-  __shared__ float red_out[NT];
+  __shared__ float red_in[2][2 * NT];         // per A buffer: the prologue converts two tiles back to back
+  __shared__ float red_out[2][NT];            // per accumulator: consecutive read-outs alternate
+  __shared__ float nin_row[2][kTcThreads];    // input norm of each group, per A buffer
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const int h = tid >> 7;
-  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += NT) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
+  for (int i = tid; i < (int)(2 * B_BYTES / 16); i += x6::kThreads) reinterpret_cast<uint4 *>(sB)[i] = bmat[i];
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                  "r"(NCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    for (int u = 0; u < 2; u++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&done[u])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&ready[u])), "n"(NT));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&drain)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   // B was written by ordinary stores: make it visible to the tensor cores
@@ -371,185 +414,203 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t mbar_a = smem_addr(&mbar);
-  const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
-  // this thread's TMEM lane (row r of A and D) in column 0
-  const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-
-  uint64_t lane_off = h ? (1ull << p.th) : 0ull;
-#pragma unroll
-  for (int i = 0; i < 5; i++)
-    if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
-  uint64_t roff[RB];
-#pragma unroll
-  for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
-  auto offset = [&](int rr) {
-    uint64_t o = lane_off;
-#pragma unroll
-    for (int j = 0; j < RB; j++)
-      if ((rr >> j) & 1) o += roff[j];
-    return o;
-  };
-  auto tile_base = [&](long long t) {
-    return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
-  };
-  const LaneExchange xch(p, lane);
-
-  // tile t into staging area u: this thread's 16 chunks, one commit group per
-  // tile (empty past the last tile, so the group count stays uniform)
-  auto stage_in = [&](long long t, int u) {
-    if (t < p.n_tiles) {
-      const uint64_t b = tile_base(t);
-      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
-#pragma unroll
-      for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + b + offset(q));
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  // tile t (staged in area u) -> A buffer u: exchange, row scale, FP16
-  // hi/lo split, tcgen05.st; refills area u with tile t + 2 G; returns the
-  // row's input norm (both halves)
   const long long G = gridDim.x;
-  auto convert = [&](long long t, int u) -> float {
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-    float4 v[NV];
-    const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
-#pragma unroll
-    for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
-    xch.run<NV>(v);
-    // the shuffles consumed the values read back: refill this thread's own
-    // chunks of the area with tile t + 2 G
-    stage_in(t + 2 * G, u);
-    float mx = 0.f, nin = 0.f;
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-      mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
-      nin = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, nin))));
-    }
-    red_in[2 * tid] = mx;
-    red_in[2 * tid + 1] = nin;
-    __syncthreads();
-    mx = fmaxf(mx, red_in[2 * (tid ^ kTcThreads)]);
-    nin += red_in[2 * (tid ^ kTcThreads) + 1];
-    int e = 0;
-    if (mx > 0.f) frexpf(mx, &e);
-    const float sc = ldexpf(1.f, -e);
-    // slot 2 q + c (register q, element c) holds K = 64 h + 4 q + 2 c (re) and
-    // + 1 (im): column 32 h + 2 q + c of its half
-    uint32_t hi[32], lo[32];
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-      const float x[4] = {v[q].x * sc, v[q].y * sc, v[q].z * sc, v[q].w * sc};
-#pragma unroll
-      for (int c = 0; c < 2; c++) {
-        const __half2 hh = __floats2half2_rn(x[2 * c], x[2 * c + 1]);
-        const float2 hf = __half22float2(hh);
-        hi[2 * q + c] = *reinterpret_cast<const uint32_t *>(&hh);
-        lo[2 * q + c] = pack_half2(x[2 * c] - hf.x, x[2 * c + 1] - hf.y);
-      }
-    }
-    const uint32_t acol = lane_base + COL_A + 128u * (uint32_t)u + 32u * (uint32_t)h;
-    TmemSt<32>::run(acol, hi);
-    TmemSt<32>::run(acol + 64, lo);
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    return nin;
-  };
-  // the MMAs of the tile in A buffer u (one thread): D = A B^T, large and
-  // small products in their own columns; completion on the mbarrier
-  auto issue = [&](int u) {
-    if (tid == 0) {
-      const uint32_t a_hi = tmem + COL_A + 128u * (uint32_t)u, a_lo = a_hi + 64u;
-#pragma unroll
-      for (int ks = 0; ks < KR / 16; ks++) {
-        const uint32_t koff = (uint32_t)ks * 2u * LBO;
-        const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
-        const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
-        const uint32_t acc = ks > 0 ? 1u : 0u;
-        mma_f16_ta(tmem, a_hi + 8u * ks, dbh, IDESC, acc);
-        mma_f16_ta(tmem + KR, a_hi + 8u * ks, dbl, IDESC, acc);
-        mma_f16_ta(tmem + KR, a_lo + 8u * ks, dbh, IDESC, 1u);
-      }
-      if (!p.withhold_commit) mma_commit(mbar_a);
-    }
-  };
-  auto publish = [&]() {
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-  };
 
-  uint32_t phase = 0;
-  bool aborted = false;
-  long long tile = blockIdx.x;
-  stage_in(tile, 0);
-  stage_in(tile + G, 1);
-  float nin_cur = 0.f, nin_next = 0.f;
-  if (tile < p.n_tiles) nin_cur = convert(tile, 0);
-  publish();
-  if (tile < p.n_tiles) issue(0);
-  for (int it = 0; tile < p.n_tiles; tile += G, it++) {
-    const int u = it & 1;
-    // the next tile into the other A buffer while this tile's MMAs run
-    const bool more = tile + G < p.n_tiles;  // uniform over the CTA
-    if (more) nin_next = convert(tile + G, u ^ 1);
-    const bool ok = mbar_wait(mbar_a, phase);
-    phase ^= 1;
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) atomicExch(err, 1);
-      aborted = true;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t cb = lane_base + 64u * (uint32_t)h;
-    float nout = 0.f;
+  if (warp == NT / 32) {
+    // ---- the MMA warp: one thread issues, tile after tile ----
+    if (lane == 0) {
+      const uint32_t b_hi = smem_addr(sB), b_lo = smem_addr(sB + B_BYTES);
+      uint32_t pr0 = 0, pr1 = 0;
+      int it = 0;
+      for (long long t = blockIdx.x; t < p.n_tiles; t += G, it++) {
+        const int u = it & 1;
+        if (!mbar_wait(smem_addr(&ready[u]), u ? pr1 : pr0)) {
+          atomicExch(err, 1);
+          break;
+        }
+        if (u) pr1 ^= 1;
+        else pr0 ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t d = tmem + 128u * (uint32_t)u;
+        const uint32_t a_hi = tmem + COL_A + 128u * (uint32_t)u, a_lo = a_hi + 64u;
 #pragma unroll
-    for (int hh = 0; hh < 4; hh++) {
-      uint32_t rb[16], rs[16];
-      TmemLd<16>::run(cb + 16 * hh, rb);
-      TmemLd<16>::run(cb + KR + 16 * hh, rs);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-      for (int i = 0; i < 16; i++) {
-        const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
-        nout = fmaf(y, y, nout);
+        for (int ks = 0; ks < KR / 16; ks++) {
+          const uint32_t koff = (uint32_t)ks * 2u * LBO;
+          const uint64_t dbh = make_desc(b_hi + koff, LBO, SBO);
+          const uint64_t dbl = make_desc(b_lo + koff, LBO, SBO);
+          mma_f16_ta(d, a_hi + 8u * ks, dbh, IDESC, ks > 0 ? 1u : 0u);
+          mma_f16_ta(d, a_hi + 8u * ks, dbl, IDESC, 1u);
+          mma_f16_ta(d, a_lo + 8u * ks, dbh, IDESC, 1u);
+        }
+        if (!p.withhold_commit) mma_commit(smem_addr(&done[u]));
       }
+      // every MMA this thread issued has completed once this commit arrives
+      mma_commit(smem_addr(&drain));
+      mbar_wait(smem_addr(&drain), 0);
     }
-    red_out[tid] = nout;
-    __syncthreads();
-    nout += red_out[tid ^ kTcThreads];
-    const float f = nout > 0.f ? sqrtf(nin_cur / nout) : 1.f;
-    const uint64_t cur_base = tile_base(tile);
+  } else {
+    // ---- the converting warps ----
+    const int h = tid >> 7;
+    const int r = tid & 127;
+    // this thread's TMEM lane (row r of A and D) in column 0
+    const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    uint64_t lane_off = h ? (1ull << p.part_bit[0]) : 0ull;
 #pragma unroll
-    for (int hh = 0; hh < 4; hh++) {
-      uint32_t rb[16], rs[16];
-      TmemLd<16>::run(cb + 16 * hh, rb);
-      TmemLd<16>::run(cb + KR + 16 * hh, rs);
+    for (int i = 0; i < 5; i++)
+      if ((lane >> i) & 1) lane_off += 1ull << p.lbit[i];
+    uint64_t roff[RB];
+#pragma unroll
+    for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
+    auto offset_from = [&](uint64_t o, int rr) {
+#pragma unroll
+      for (int j = 0; j < RB; j++)
+        if ((rr >> j) & 1) o += roff[j];
+      return o;
+    };
+    auto offset = [&](int rr) { return offset_from(lane_off, rr); };
+    // after the element bit's exchange alone (nswb = 0, la >= 0): this
+    // lane's la bit addresses bit 0, and the element addresses lbit[la]
+    const bool direct = p.nswb == 0;
+    const bool la_up = p.la >= 0 && ((lane >> p.la) & 1);
+    const uint64_t lane_post =
+        p.la >= 0 ? lane_off - (la_up ? (1ull << p.lbit[p.la]) : 0ull) + (la_up ? 1ull : 0ull) : lane_off;
+    const uint64_t e_off = p.la >= 0 ? (1ull << p.lbit[p.la]) : 1ull;
+    auto tile_base = [&](long long t) {
+      return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
+    };
+    const LaneExchange xch(p, lane);
+
+    // tile t into staging area u: this thread's 16 chunks, one commit group
+    // per tile (empty past the last tile, so the group count stays uniform)
+    auto stage_in = [&](long long t, int u) {
+      if (t < p.n_tiles) {
+        const uint64_t b = tile_base(t);
+        const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+        for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + b + offset(q));
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // tile t (staged in area u) -> A buffer u: exchange, row scale, FP16
+    // hi/lo split, tcgen05.st; refills area u with tile t + 2 G; the row's
+    // input norm (both halves) goes to nin_row[u]; then arrives on ready[u]
+    auto convert = [&](long long t, int u) {
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      float4 v[NV];
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+#pragma unroll
+      for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
+      xch.run<NV>(v);
+      // the shuffles consumed the values read back: refill this thread's own
+      // chunks of the area with tile t + 2 G
+      stage_in(t + 2 * G, u);
+      // row max and squared norm in four independent chains
+      float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        m4[q & 3] = fmaxf(m4[q & 3], fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+        s4[q & 3] = fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, fmaf(v[q].z, v[q].z, fmaf(v[q].w, v[q].w, s4[q & 3]))));
+      }
+      float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
+      float nin = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      red_in[u][2 * tid] = mx;
+      red_in[u][2 * tid + 1] = nin;
+      x6::conv_sync();
+      mx = fmaxf(mx, red_in[u][2 * (tid ^ kTcThreads)]);
+      nin += red_in[u][2 * (tid ^ kTcThreads) + 1];
+      if (h == 0) nin_row[u][r] = nin;
+      int e = 0;
+      if (mx > 0.f) frexpf(mx, &e);
+      const float sc = ldexpf(1.f, -e);
+      // slot 2 q + c (register q, element c) holds K = 64 h + 4 q + 2 c (re)
+      // and + 1 (im): column 32 h + 2 q + c of its half
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        const float x[4] = {v[q].x * sc, v[q].y * sc, v[q].z * sc, v[q].w * sc};
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+          const __half2 hh = __floats2half2_rn(x[2 * c], x[2 * c + 1]);
+          const float2 hf = __half22float2(hh);
+          hi[2 * q + c] = *reinterpret_cast<const uint32_t *>(&hh);
+          lo[2 * q + c] = pack_half2(x[2 * c] - hf.x, x[2 * c + 1] - hf.y);
+        }
+      }
+      const uint32_t acol = lane_base + COL_A + 128u * (uint32_t)u + 32u * (uint32_t)h;
+      TmemSt<32>::run(acol, hi);
+      TmemSt<32>::run(acol + 64, lo);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      x6::mbar_arrive(smem_addr(&ready[u]));
+    };
+
+    uint32_t pd0 = 0, pd1 = 0;  // parity each accumulator's barrier waits for next
+    long long tile = blockIdx.x;
+    stage_in(tile, 0);
+    stage_in(tile + G, 1);
+    if (tile < p.n_tiles) convert(tile, 0);
+    if (tile + G < p.n_tiles) convert(tile + G, 1);
+    for (int it = 0; tile < p.n_tiles; tile += G, it++) {
+      const int u = it & 1;
+      const bool ok = mbar_wait(smem_addr(&done[u]), u ? pd1 : pd0);
+      if (u) pd1 ^= 1;
+      else pd0 ^= 1;
+      if (!x6::conv_and(ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t y32[64];
+      TmemLd<64>::run(lane_base + 128u * (uint32_t)u + 64u * (uint32_t)h, y32);
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      float4 y[4];
+      float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < 4; q++)
-        y[q] = make_float4((__uint_as_float(rb[4 * q]) + __uint_as_float(rs[4 * q])) * f,
-                           (__uint_as_float(rb[4 * q + 1]) + __uint_as_float(rs[4 * q + 1])) * f,
-                           (__uint_as_float(rb[4 * q + 2]) + __uint_as_float(rs[4 * q + 2])) * f,
-                           (__uint_as_float(rb[4 * q + 3]) + __uint_as_float(rs[4 * q + 3])) * f);
-      xch.run<4>(y);
+      for (int i = 0; i < 64; i++) o4[i & 3] = fmaf(__uint_as_float(y32[i]), __uint_as_float(y32[i]), o4[i & 3]);
+      float nout = (o4[0] + o4[1]) + (o4[2] + o4[3]);
+      red_out[u][tid] = nout;
+      x6::conv_sync();
+      nout += red_out[u][tid ^ kTcThreads];
+      const float nin = nin_row[u][r];
+      const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
+      const uint64_t cur_base = tile_base(tile);
+      if (direct) {
+        // no lane/register exchange to undo: slot halves straight to memory
+        float2 *dst = a + cur_base;
 #pragma unroll
-      for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
+        for (int q = 0; q < NV; q++) {
+          const float2 y0 = make_float2(__uint_as_float(y32[4 * q]) * f, __uint_as_float(y32[4 * q + 1]) * f);
+          const float2 y1 = make_float2(__uint_as_float(y32[4 * q + 2]) * f, __uint_as_float(y32[4 * q + 3]) * f);
+          const uint64_t o = offset_from(lane_post, q);
+          if (p.la >= 0) {
+            dst[o] = y0;
+            dst[o + e_off] = y1;
+          } else {
+            *reinterpret_cast<float4 *>(dst + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int hh = 0; hh < 4; hh++) {
+          float4 y[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            y[q] = make_float4(__uint_as_float(y32[16 * hh + 4 * q]) * f,
+                               __uint_as_float(y32[16 * hh + 4 * q + 1]) * f,
+                               __uint_as_float(y32[16 * hh + 4 * q + 2]) * f,
+                               __uint_as_float(y32[16 * hh + 4 * q + 3]) * f);
+          xch.run<4>(y);
+#pragma unroll
+          for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
+        }
+      }
+      // tile + 2 G into the A buffer (and, for the MMA warp, the accumulator)
+      // this tile has finished with
+      if (tile + 2 * G < p.n_tiles) convert(tile + 2 * G, u);
     }
-    // every thread has read the products and written the next A buffer
-    publish();
-    if (more) issue(u ^ 1);
-    nin_cur = nin_next;
+    asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");  // copies still in flight
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (aborted) {
-    // MMAs may still be in flight: one more commit tracks all of them; wait
-    // for it (bounded) before the columns are returned
-    if (tid == 0) mma_commit(mbar_a);
-    mbar_wait(mbar_a, phase ^ 1);
-  }
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
@@ -564,7 +625,8 @@ void fill_xparam(int K, int n, const Block &b, const TcXLayout &x, TcXParam &p) 
   p.la = x.la;
   p.nswb = x.nswb;
   for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
-  p.th = x.th;
+  p.part_bit[0] = x.part_bit[0];
+  p.part_bit[1] = x.part_bit[1];
   p.withhold_commit = b.withhold_commit ? 1 : 0;
 }
 
@@ -610,7 +672,7 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
   if (configured != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    if (resident_ctas((const void *)k_dense_tc16x6, 2 * kTcThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    if (resident_ctas((const void *)k_dense_tc16x6, x6::kThreads, smem) < 1) return cudaErrorInvalidConfiguration;
     configured = dev;
   }
   const int grid = tc_grid((long long)dev_info().sms, p.n_tiles, b.tc_max_ctas);  // one CTA per SM
@@ -618,7 +680,7 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
     shape->tiles = p.n_tiles;
     shape->ctas = grid;
   }
-  k_dense_tc16x6<<<grid, 2 * kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  k_dense_tc16x6<<<grid, x6::kThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -656,8 +718,8 @@ bool tc_exchange_pays(const Block &b) {
 
 bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
   if (b.kind == BK_DENSE && b.k == 6 && !(b.cmask & 1ull)) {
-    // two threads per group: each half is a 5-target exchange over the five
-    // lower targets with the highest one fixed (like a control) per half
+    // two threads per group: each part is a 5-target exchange over the five
+    // lower targets with the highest fixed (like a control) per part
     Block b5;
     b5.kind = BK_DENSE;
     b5.k = 5;
@@ -665,11 +727,12 @@ bool tc_exchange_layout(int n, const Block &b, TcXLayout &x) {
     b5.cmask = b.cmask | (1ull << b.q[5]);
     b5.nctrl = b.nctrl + 1;
     if (!tc_exchange_layout(n, b5, x)) return false;
-    x.th = b.q[5];
+    x.part_bit[0] = b.q[5];
+    x.part_bit[1] = -1;
     x.slot_mat[5] = 5;
     return true;
   }
-  x.th = -1;
+  x.part_bit[0] = x.part_bit[1] = -1;
   if (b.kind != BK_DENSE || (b.k != 4 && b.k != 5) || (b.cmask & 1ull)) return false;
   const int K = b.k;
   if (n - K - b.nctrl < 7) return false;  // whole tiles of 128 groups

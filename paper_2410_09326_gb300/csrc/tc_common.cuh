@@ -101,6 +101,15 @@ inline int tc_grid(long long wave, long long tiles, int max_ctas) {
 // 32 consecutive 32-bit columns of this thread's TMEM lane from registers
 // (the warp writes its 32-lane quadrant); complete with tcgen05.wait::st.
 template <int N> struct TmemSt;
+template <> struct TmemSt<16> {
+  __device__ static void run(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+  }
+};
 template <> struct TmemSt<32> {
   __device__ static void run(uint32_t taddr, const uint32_t *r) {
     asm volatile(

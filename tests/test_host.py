@@ -369,7 +369,8 @@ def exchange_emulation(lay, k):
 def test_lane_exchange_layout_index_arithmetic():
     """The tensor-core lane-exchange layout (qs_tc_exchange_layout), checked
     by emulating a warp on the CPU for 3000 random blocks (4..6 targets,
-    biased to low bits, 0..2 controls, n up to 34): the element, lane and
+    biased to low bits, 0..2 controls, n up to 34) and 1000 6-target blocks
+    with uniformly placed bits: the element, lane and
     register bits are exactly the warp's sub-cube (targets + five lowest free
     bits), so every amplitude of a sub-cube is loaded once; after the
     exchanges every lane holds one group -- one assignment of the free bits
@@ -378,14 +379,16 @@ def test_lane_exchange_layout_index_arithmetic():
     layout; the layout applies exactly when bit 0 is not a control and 7 or
     more free bits remain."""
     rng = cg.SplitMix64(4242)
-    applied = 0
-    for _ in range(3000):
-        k = 4 + rng.randint(3)
+    applied = direct_checked = 0
+    for trial in range(4000):
+        # the last 1000: 6-target blocks with uniformly placed bits (mostly
+        # layouts without lane/register exchanges, the direct-store case)
+        k = 6 if trial >= 3000 else 4 + rng.randint(3)
         nctrl = rng.randint(3)
         n = min(34, k + nctrl + 5 + rng.randint(12))
         chosen = []
         while len(chosen) < k + nctrl:
-            q = rng.randint(n) if rng.randint(3) == 0 else rng.randint(min(n, 8))
+            q = rng.randint(n) if trial >= 3000 or rng.randint(3) == 0 else rng.randint(min(n, 8))
             if q not in chosen:
                 chosen.append(q)
         targets = sorted(chosen[:k])
@@ -403,9 +406,9 @@ def test_lane_exchange_layout_index_arithmetic():
         pos = [0] + list(lay.lane_bits) + list(lay.reg_bits[:nrb])
         assert sorted(pos) == cube, (targets, ctrls, pos, cube)
         if k == 6:
-            assert lay.half_bit == targets[5] and lay.slot_target[5] == 5
+            assert list(lay.part_bits) == [targets[5], -1] and lay.slot_target[5] == 5
         else:
-            assert lay.half_bit == -1
+            assert list(lay.part_bits) == [-1, -1]
         assert 0 <= lay.nswb <= 2
         off, run = exchange_emulation(lay, k)
         after = run(off)
@@ -413,7 +416,7 @@ def test_lane_exchange_layout_index_arithmetic():
         nv = off.shape[1]
         rho = (np.arange(2)[None, :] + 2 * np.arange(nv)[:, None])   # slot of (register, element)
         slot_off = np.zeros_like(rho)
-        for sb in range(min(k, 5)):
+        for sb in range(len(inner)):
             slot_off += ((rho >> sb) & 1) << targets[lay.slot_target[sb]]
         groups = after[:, 0, 0]
         assert np.all(groups & tmask == 0)
@@ -421,7 +424,24 @@ def test_lane_exchange_layout_index_arithmetic():
         assert np.array_equal(after, groups[:, None, None] + slot_off[None, :, :])
         back = np.concatenate([run(after[:, c:c + 4, :]) for c in range(0, nv, 4)], axis=1)
         assert np.array_equal(back, off)
-    assert applied > 2000
+        if k == 6 and lay.nswb == 0:
+            # the 6-target kernel's direct stores (no exchange back): lane
+            # l's register q element e goes to lane_post(l) + reg_off(q) +
+            # e * e_off, where the element's exchange moved the la lane bit
+            # to bit 0 and the element to lane_bits[la]
+            lanes = np.arange(32, dtype=np.int64)
+            lane_off = sum(((lanes >> i) & 1) << int(lay.lane_bits[i]) for i in range(5))
+            if lay.la >= 0:
+                up = (lanes >> lay.la) & 1
+                lane_post = lane_off - (up << int(lay.lane_bits[lay.la])) + up
+                e_off = 1 << int(lay.lane_bits[lay.la])
+            else:
+                lane_post, e_off = lane_off, 1
+            reg_off = sum(((np.arange(nv) >> j) & 1) << int(lay.reg_bits[j]) for j in range(nrb))
+            direct = lane_post[:, None, None] + reg_off[None, :, None] + np.arange(2)[None, None, :] * e_off
+            assert np.array_equal(direct, after), (targets, ctrls)
+            direct_checked += 1
+    assert applied > 2500 and direct_checked > 150
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
