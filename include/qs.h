@@ -302,6 +302,16 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
                         const qs_opts *opts, uint64_t *flags_out, double *predicted_ms);
 
 /*
+ * The same model for one given flag set (Sec. III-A: the profile's estimate
+ * of what a set of passes would cost): plans `flags` on the host and writes
+ * the predicted device milliseconds (sum over blocks of bytes / class
+ * throughput from `table`, or the compiled-in priors where NULL or
+ * unmeasured, plus a launch gap per block). Host only.
+ */
+qs_status qs_pgo_predict(int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                         const qs_class_table *table, const qs_opts *opts, double *predicted_ms);
+
+/*
  * The host passes alone (virtual swap, fusion, classification), without a
  * GPU: the plan qs_apply_circuit would launch for a state of n qubits whose
  * map is *perm_inout (n entries, updated for absorbed SWAPs). Fills up to cap

@@ -139,6 +139,9 @@ def load(build_if_missing=False):
         "qs_pgo_select": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, sz, ctypes.POINTER(qs_class_table),
                                          ctypes.POINTER(qs_opts), ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_double)]),
+        "qs_pgo_predict": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, sz, ctypes.c_uint64,
+                                          ctypes.POINTER(qs_class_table), ctypes.POINTER(qs_opts),
+                                          ctypes.POINTER(ctypes.c_double)]),
         "qs_get_perm": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int8)]),
         "qs_measure_probs": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                             ctypes.POINTER(ctypes.c_double)]),
@@ -283,6 +286,17 @@ def qs_pgo_select(n, gates, dtype=QS_C64, table=None, opts=None):
                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(f),
                                 ctypes.byref(ms)))
     return f.value, ms.value
+
+
+def qs_pgo_predict(n, gates, flags, dtype=QS_C64, table=None, opts=None):
+    """Host-only plan-time prediction (ms) of one flag set from a class table
+    (None: the compiled-in priors)."""
+    gates = np.ascontiguousarray(gates, dtype=GATE_DTYPE)
+    ms = ctypes.c_double(0)
+    _check(load().qs_pgo_predict(n, dtype, gates.ctypes.data_as(ctypes.c_void_p), gates.size, flags,
+                                 ctypes.byref(table) if table is not None else None,
+                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(ms)))
+    return ms.value
 
 
 def qs_profile_reset(st):

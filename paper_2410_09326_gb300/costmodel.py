@@ -13,8 +13,8 @@ import numpy as np
 import circuitgen as cg
 
 from . import (QS_C64, QS_DIAG, QS_FUSE, QS_FUSE_K, QS_PROFILE, QS_TC, QS_TILE, QS_VSWAP, gates_to_array,
-               qs_alloc_state, qs_apply_circuit, qs_block_features, qs_free_state, qs_profile,
-               qs_set_basis)
+               qs_alloc_state, qs_apply_circuit, qs_block_features, qs_free_state, qs_mlp_predict, qs_plan,
+               qs_profile, qs_set_basis)
 
 # flag sets profiled for training: every kernel class the selector can choose
 TRAIN_FLAGS = [0, QS_VSWAP] + [QS_VSWAP | QS_FUSE | QS_FUSE_K(k) | QS_DIAG for k in (2, 3, 4, 5, 6)] + \
@@ -82,6 +82,19 @@ def training_circuits(count, n_lo=20, n_hi=30, index0=0):
             gates, _ = cg.qaoa_maxcut(n, 1 + rng.randint(4), rng)
             out.append((n, gates))
     return out
+
+
+def mlp_plan_ms(m, n, gates, flags):
+    """The network's prediction of one flag set's device time: the planned
+    blocks' predicted times plus the activator's launch gap per block."""
+    recs, _, _ = qs_plan(n, gates_to_array(gates), flags)
+    # a tile pass's member blocks follow it with its index; only the pass runs
+    seen = set()
+    recs = [r for r in recs if not (r.index in seen or seen.add(r.index))]
+    if not recs:
+        return 0.0
+    y = qs_mlp_predict(m, qs_block_features(n, recs))
+    return float(np.exp(y.astype(np.float64)).sum() + 0.004 * len(recs))
 
 
 def measure_candidates(n, gates, candidates, repeats=2):

@@ -468,6 +468,26 @@ qs_status qs_pgo_select(int n, qs_dtype dtype, const qs_gate *gates, size_t n_ga
   return QS_OK;
 }
 
+qs_status qs_pgo_predict(int n, qs_dtype dtype, const qs_gate *gates, size_t n_gates, uint64_t flags,
+                         const qs_class_table *table, const qs_opts *opts, double *predicted_ms) {
+  if (!predicted_ms || (n_gates && !gates)) return fail(QS_EINVAL, "qs_pgo_predict: null argument");
+  if (n < 1 || n > QS_MAX_QUBITS) return fail(QS_EINVAL, "qs_pgo_predict: qubit count out of range");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "qs_pgo_predict: unknown dtype");
+  if (flags & (QS_PGO_RULES | QS_PGO_MEASURED)) return fail(QS_EINVAL, "qs_pgo_predict: give explicit pass flags");
+  qs_opts o;
+  if (opts) o = *opts;
+  else qs_default_opts(&o);
+  std::vector<Block> plan;
+  PlanStats stats;
+  std::string err;
+  int8_t perm[QS_MAX_QUBITS];
+  for (int q = 0; q < n; q++) perm[q] = (int8_t)q;
+  qs_status s = build_plan(n, gates, n_gates, flags, o, perm, plan, stats, err, dtype == QS_C128);
+  if (s != QS_OK) return fail(s, "qs_pgo_predict: " + err);
+  *predicted_ms = predict_plan_ms(plan, n, dtype == QS_C128 ? 16 : 8, table, o.peak_gbs > 0 ? o.peak_gbs : 6688.8);
+  return QS_OK;
+}
+
 qs_status qs_fold_rotations(int n, const qs_gate *in, size_t n_in, qs_gate *out, size_t cap, size_t *n_out) {
   if (n < 1 || n > QS_MAX_QUBITS || (n_in && !in) || !n_out) return fail(QS_EINVAL, "qs_fold_rotations: bad arguments");
   std::vector<Block> plan;

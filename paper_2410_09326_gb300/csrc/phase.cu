@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase(T *__restrict__ a, cons
         g.x = __shfl_sync(0xffffffffu, fb.x, src);
         g.y = __shfl_sync(0xffffffffu, fb.y, src);
         const int o = 2 * lane + 64 * it;
-        const T w0 = cmul(cmul(ltab[o], fa0), g), w1 = cmul(cmul(ltab[o + 1], fa1), g);
+        // the two table entries of this lane's pair in one 16-byte load
+        const float4 lt = *reinterpret_cast<const float4 *>(ltab + o);
+        const T w0 = cmul(cmul(make_float2(lt.x, lt.y), fa0), g), w1 = cmul(cmul(make_float2(lt.z, lt.w), fa1), g);
         float4 y;
         y.x = fmaf(w0.x, v[it].x, -w0.y * v[it].y);
         y.y = fmaf(w0.x, v[it].y, w0.y * v[it].x);

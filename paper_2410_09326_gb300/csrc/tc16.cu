@@ -140,13 +140,16 @@ __global__ void __launch_bounds__(kTcThreads * tc16_rows<K>(), Tc16Occ<K>::value
   gather(tile);
 
   for (; tile < p.n_tiles; tile += gridDim.x) {
-    // row scale: largest component into [0.5, 1)
-    float mx = 0.f, nin = 0.f;
+    // row scale: largest component into [0.5, 1); max and norm in four
+    // independent chains
+    float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < DH; u++) {
-      mx = fmaxf(mx, fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
-      nin = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, nin));
+      m4[u & 3] = fmaxf(m4[u & 3], fmaxf(fabsf(v[u].x), fabsf(v[u].y)));
+      s4[u & 3] = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, s4[u & 3]));
     }
+    float mx = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
+    float nin = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     if constexpr (TPR > 1) {
       red_in[2 * tid] = mx;
       red_in[2 * tid + 1] = nin;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(kTcThreads * tc16_rows<K>(), Tc16Occ<K>::value
     const uint32_t col0 = (uint32_t)(2 * s0);  // this thread's first column
     // pass 1: norm of the computed group (large + small products), 16
     // columns (8 amplitudes) at a time to keep registers free
-    float nout = 0.f;
+    float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int hh = 0; hh < 2 * DH / 16; hh++) {
       uint32_t rb[16], rs[16];
@@ -220,9 +223,10 @@ __global__ void __launch_bounds__(kTcThreads * tc16_rows<K>(), Tc16Occ<K>::value
 #pragma unroll
       for (int i = 0; i < 16; i++) {
         const float y = __uint_as_float(rb[i]) + __uint_as_float(rs[i]);
-        nout = fmaf(y, y, nout);
+        o4[i & 3] = fmaf(y, y, o4[i & 3]);
       }
     }
+    float nout = (o4[0] + o4[1]) + (o4[2] + o4[3]);
     if constexpr (TPR > 1) {
       red_out[tid] = nout;
       __syncthreads();

@@ -55,42 +55,65 @@ def test_training_fits_a_known_function():
         qs.qs_mlp_free(m)
 
 
-def uniform_table(gbs=6000.0):
-    """A class table in which every kernel class moves bytes at the same rate:
-    the activator then ranks plans by algorithmic bytes alone (no profile)."""
-    t = qs.qs_class_table()
-    for c in range(qs.QS_N_CLASSES):
-        t.bytes[c] = gbs * 1e6
-        t.ms[c] = 1.0
-        t.count[c] = 1
-    return t
+def low_heavy(n, layers, rng):
+    """Layers of U3 on qubits 0..5, a CX chain among them and one CX from a
+    low qubit to a random high one: nearly every gate on the lowest bits."""
+    g = []
+    for _ in range(layers):
+        g += [("u3", [q], [rng.uniform(0, 6.28) for _ in range(3)]) for q in range(6)]
+        g += [("cx", [q, q + 1]) for q in range(5)]
+        g.append(("cx", [rng.randint(6), 6 + rng.randint(n - 6)]))
+    return g
 
 
-def test_learned_selection_gains_over_a_profile_free_model():
-    """Train on profiled blocks of seeded circuits (random layered, QFT, GHZ,
-    QAOA; n = 18..23), then pick flags for unseen GHZ / QFT / random circuits
-    at n = 24 without running them. The method without the network ranks
-    candidate plans by algorithmic bytes alone; the network must choose within
-    15% of brute force over the candidates and do better than bytes on
-    average. The hand-set per-class priors are reported beside it."""
-    train = costmodel.training_circuits(30, n_lo=18, n_hi=23, index0=100)
+def ctrl_heavy(n, layers, rng):
+    """Layers of RY on every qubit and n/3 CCX / CSWAP / CU3 on random qubits."""
+    g = []
+    for _ in range(layers):
+        g += [("ry", [q], [rng.uniform(0, 6.28)]) for q in range(n)]
+        for _ in range(n // 3):
+            a, b, c = rng.shuffle(list(range(n)))[:3]
+            nm = ["ccx", "cswap", "cu3"][rng.randint(3)]
+            g.append((nm, [a, b], [rng.uniform(0, 6.28) for _ in range(3)]) if nm == "cu3" else (nm, [a, b, c]))
+    return g
+
+
+def test_learned_selection_gains_over_the_priors():
+    """What the trained network gains over the selector without it (the
+    compiled-in per-class priors, Sec. III-A's open profile-to-flags mapping).
+    Train on profiled blocks of seeded layered-random, QFT, GHZ and QAOA
+    circuits (n = 18..26), then pick flags for circuit families it has not
+    seen -- low-target-heavy layers, controlled-gate-heavy layers, a random
+    circuit and QAOA, n = 24..26 -- without running them, against brute force
+    over the 12 candidate flag sets measured on this GPU. The priors charge
+    a tile pass a fixed fraction of HBM bandwidth whatever its gate count and
+    so choose tile passes for the low-target-heavy circuits (measured 2-3x
+    slower than the best); the network, which sees the gate count, does not.
+    Asserted: the network's mean regret is below the priors' by at least
+    0.15, its worst regret within 25% of brute force, and its predictions of
+    the candidates' device times are closer to the measured ones."""
+    train = costmodel.training_circuits(40, n_lo=18, n_hi=26, index0=100)
     x, y = costmodel.build_dataset(train)
-    assert len(y) > 1000
+    assert len(y) > 20000
     m = qs.qs_mlp_create(11)
     try:
         qs.qs_mlp_train(m, x, y, epochs=40, batch=256, lr=2e-3, seed=2)
-        n = 24
-        c = cg.benchmark_circuits(n=n, index=5)
-        unseen = {"ghz": c["ghz"][1], "qft": c["qft"][1], "random": c["random"][1]}
-        flat = uniform_table()
+        rng = cg.SplitMix64(777)
+        held = {}
+        for n in (24, 25, 26):
+            held[f"low_heavy_n{n}"] = (n, low_heavy(n, 40, rng))
+        held["ctrl_heavy_n24"] = (24, ctrl_heavy(24, 6, rng))
+        held["random_n25"] = (25, cg.random_layered(25, 20, rng, swap_frac=0.05))
+        held["qaoa_n24"] = (24, cg.qaoa_maxcut(24, 3, rng)[0])
+        held["qaoa_n26"] = (26, cg.qaoa_maxcut(26, 3, rng)[0])
+        cands = [qs.QS_PLAIN, qs.QS_VSWAP] + \
+                [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)] + \
+                [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | qs.QS_TC for k in (4, 5, 6)] + \
+                [qs.QS_VSWAP | qs.QS_TILE]
         report = {}
-        for name, gates in unseen.items():
+        for name, (n, gates) in held.items():
             arr = qs.gates_to_array(gates)
-            fx, fy, _ = costmodel.profile_blocks(n, gates, qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(5) | qs.QS_DIAG |
-                                                 qs.QS_TC)
-            cands = [qs.QS_PLAIN] + [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG for k in range(1, 7)] + \
-                    [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | qs.QS_TC for k in (4, 5)]
-            meas = costmodel.measure_candidates(n, gates, cands)
+            meas = costmodel.measure_candidates(n, gates, cands, repeats=2)
             best = min(meas.values())
 
             def regret(f):
@@ -99,15 +122,17 @@ def test_learned_selection_gains_over_a_profile_free_model():
                     t = costmodel.measure_candidates(n, gates, [f])[f]
                 return t / best
 
+            err_mlp = np.mean([abs(math.log(costmodel.mlp_plan_ms(m, n, gates, f) / meas[f])) for f in cands])
+            err_pri = np.mean([abs(math.log(qs.qs_pgo_predict(n, arr, f) / meas[f])) for f in cands])
             report[name] = {"mlp": regret(qs.qs_pgo_select_mlp(m, n, arr)[0]),
-                            "bytes_only": regret(qs.qs_pgo_select(n, arr, table=flat)[0]),
                             "priors": regret(qs.qs_pgo_select(n, arr)[0]),
-                            "block_log_err_mlp": float(np.mean(np.abs(qs.qs_mlp_predict(m, fx) - fy)))}
+                            "plan_log_err_mlp": float(err_mlp), "plan_log_err_priors": float(err_pri)}
         print(report)
         r_mlp = [r["mlp"] for r in report.values()]
-        r_bytes = [r["bytes_only"] for r in report.values()]
-        assert max(r_mlp) <= 1.15, report
-        assert np.mean(r_mlp) < np.mean(r_bytes), report
-        assert np.mean([r["block_log_err_mlp"] for r in report.values()]) < 0.35, report
+        r_pri = [r["priors"] for r in report.values()]
+        assert np.mean(r_mlp) <= np.mean(r_pri) - 0.15, report
+        assert max(r_mlp) <= 1.25, report
+        assert np.mean([r["plan_log_err_mlp"] for r in report.values()]) < \
+            np.mean([r["plan_log_err_priors"] for r in report.values()]), report
     finally:
         qs.qs_mlp_free(m)

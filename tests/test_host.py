@@ -494,6 +494,25 @@ def test_measured_select_with_priors_prefers_wide_tensor_core_blocks():
     assert not flags & qs.QS_VSWAP and flags & qs.QS_FUSE
 
 
+def test_pgo_predict_matches_the_selectors_estimate():
+    """qs_pgo_predict of the flag set qs_pgo_select chose reproduces the
+    selector's own predicted time (priors and a class table), and no
+    candidate the selector considered is predicted faster."""
+    n = 24
+    gates = qs.gates_to_array(cg.benchmark_circuits(n=n)["random"][1])
+    t = qs.qs_class_table()
+    for c in range(qs.QS_N_CLASSES):
+        t.bytes[c], t.ms[c], t.count[c] = (3e9 if c % 3 else 5e9), 1.0, 1
+    for table in (None, t):
+        f, ms = qs.qs_pgo_select(n, gates, table=table)
+        assert qs.qs_pgo_predict(n, gates, f, table=table) == pytest.approx(ms, rel=1e-12)
+        others = [qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_DIAG | tc
+                  for k in range(1, 7) for tc in ((0, qs.QS_TC) if k >= 4 else (0,))]
+        assert all(qs.qs_pgo_predict(n, gates, g, table=table) >= ms * 0.999 for g in others)
+    with pytest.raises(qs.QsError):
+        qs.qs_pgo_predict(n, gates, qs.QS_PGO_RULES)
+
+
 def test_measured_select_follows_the_table():
     """A table in which every tensor-core class ran slowly steers the choice
     away from the tensor cores; one in which wide CUDA-core blocks ran fast
