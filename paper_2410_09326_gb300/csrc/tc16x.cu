@@ -333,29 +333,35 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
 // refilled with tile i + 4 by cp.async -- into the A buffer tile i used, and
 // arrives on ready[i % 2]. Warp 8 issues the MMAs: tile i once ready[i % 2]
 // says its A is written and its accumulator read out, with completion on
-// done[i % 2]. The converting warps never wait for an MMA issue and
-// synchronise among themselves only (named barrier 1). Where the layout
+// done[i % 2]. The converting warps never wait for an MMA issue, and a
+// group's two threads (warps w and w + 4) synchronise only with each other,
+// on named barrier 1 + w: the four warp pairs run independently between
+// the tile-wide mbarriers. Where the layout
 // needs no lane/register exchange (nswb = 0) the products are stored
 // without exchanging back: each lane writes its two slot halves of a
 // register as 8-byte pairs, which across the warp still cover whole runs
 // of the lowest bits. Measured on GB300 from random states at n = 28, high
 // targets: one A buffer in shared memory, register gathers 5.1 TB/s; A in
 // TMEM with staging 5.3; both double-buffered, one thread issuing 4.7;
-// warp roles 5.56; four threads per group instead of two 5.37.
+// warp roles 5.56 (four threads per group instead of two: 5.37); the row
+// reductions in independent chains and direct stores 5.87; barriers per
+// warp pair instead of all eight warps 6.01.
 namespace x6 {
 constexpr int kConv = 2 * kTcThreads;  // converting threads, two per group
 constexpr int kThreads = kConv + 32;   // + the MMA warp
-__device__ __forceinline__ void conv_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConv) : "memory"); }
-// AND of a predicate over the converting threads (named barrier 1)
-__device__ __forceinline__ bool conv_and(bool v) {
+// The two threads of a group sit in warps w and w + 4 (w = warp % 4): such a
+// pair of warps synchronises on its own named barrier 1 + w (64 threads).
+__device__ __forceinline__ void pair_sync(int w) { asm volatile("bar.sync %0, 64;" ::"r"(1 + w) : "memory"); }
+// AND of a predicate over the pair of warps
+__device__ __forceinline__ bool pair_and(int w, bool v) {
   uint32_t out;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 q, %1, 0;\n\t"
-      "bar.red.and.pred p, 1, %2, q;\n\t"
+      "bar.red.and.pred p, %2, 64, q;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(out)
-      : "r"((uint32_t)v), "n"(kConv)
+      : "r"((uint32_t)v), "r"(1 + w)
       : "memory");
   return out != 0;
 }
@@ -515,7 +521,7 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       float nin = (s4[0] + s4[1]) + (s4[2] + s4[3]);
       red_in[u][2 * tid] = mx;
       red_in[u][2 * tid + 1] = nin;
-      x6::conv_sync();
+      x6::pair_sync(warp & 3);
       mx = fmaxf(mx, red_in[u][2 * (tid ^ kTcThreads)]);
       nin += red_in[u][2 * (tid ^ kTcThreads) + 1];
       if (h == 0) nin_row[u][r] = nin;
@@ -555,8 +561,10 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       const bool ok = mbar_wait(smem_addr(&done[u]), u ? pd1 : pd0);
       if (u) pd1 ^= 1;
       else pd0 ^= 1;
-      if (!x6::conv_and(ok)) {
-        if (tid == 0) atomicExch(err, 1);
+      // a pair that gives up stops arriving on ready[]: the MMA warp's and
+      // the other pairs' bounded waits then run out as well
+      if (!x6::pair_and(warp & 3, ok)) {
+        if (lane == 0) atomicExch(err, 1);
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -568,7 +576,7 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       for (int i = 0; i < 64; i++) o4[i & 3] = fmaf(__uint_as_float(y32[i]), __uint_as_float(y32[i]), o4[i & 3]);
       float nout = (o4[0] + o4[1]) + (o4[2] + o4[3]);
       red_out[u][tid] = nout;
-      x6::conv_sync();
+      x6::pair_sync(warp & 3);
       nout += red_out[u][tid ^ kTcThreads];
       const float nin = nin_row[u][r];
       const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
