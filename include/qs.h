@@ -410,18 +410,20 @@ qs_status qs_measure_probs(qs_state *st, const int *logical_qubits, int m, doubl
  * pointers: dev_amps holds 2^n amplitudes of `dtype` in device memory
  * (16-byte aligned), phys_bits (host, m entries) names PHYSICAL bit
  * positions (bin bit j = phys_bits[j]; map logical qubits through perm
- * first), and dev_out receives 2^m doubles in device memory. The work is
- * enqueued on cuda_stream (a cudaStream_t; NULL = legacy stream) and the call
- * returns without synchronising.
- * Scratch: a fixed 4 MiB array inside the library (kept by every GPU that
- * loads it until exit) holds the per-CTA partial sums, so m is limited to
- * 0..min(n, 12); larger m returns QS_EINVAL. The call makes no cudaMalloc,
- * cudaFree or other allocating call. The first call on a device resolves the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture. All calls share the one
- * array: calls whose work overlaps on the GPU (different streams, or several
- * host threads) race and may corrupt each other's results; order them on
- * one stream.
+ * first), and dev_out receives 2^m doubles in device memory (8-byte
+ * aligned), m in 0..min(n, 26); larger m returns QS_EINVAL. The work is
+ * enqueued on cuda_stream (a cudaStream_t; NULL = legacy stream) and the
+ * call returns without synchronising.
+ * Scratch: states of 12 or more qubits need none -- the call zeroes dev_out
+ * with an asynchronous memset and the kernel accumulates into it. Smaller
+ * states keep per-CTA partial sums in a fixed 128 KiB array inside the
+ * library (kept by every GPU that loads it until exit). The call makes no
+ * cudaMalloc, cudaFree or other allocating call. The first call on a device
+ * resolves the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture. All calls
+ * on states below 12 qubits share the one array: such calls whose work
+ * overlaps on the GPU (different streams, or several host threads) race and
+ * may corrupt each other's results; order them on one stream.
  */
 qs_status qs_probs_noalloc(const void *dev_amps, int n, qs_dtype dtype, const int *phys_bits, int m,
                            double *dev_out, void *cuda_stream);

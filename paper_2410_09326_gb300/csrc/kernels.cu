@@ -718,16 +718,20 @@ cudaError_t launch_probs(const void *amps, int n, bool c128, const int *pos, int
 // Some callers cannot let a library call cudaMalloc: a serving process that
 // reserved all of its device memory up front through its own pool, or a
 // caller that must not risk the device-wide synchronisation cudaMalloc and
-// cudaFree may imply. For them the per-CTA partial histograms of the
-// probability reduction live in this fixed array instead of state-owned
-// scratch. Every GPU that loads the library keeps these 4 MiB until exit.
+// cudaFree may imply. For them, states of fewer than 12 qubits keep the
+// per-CTA partial histograms of the probability reduction in this fixed
+// array instead of state-owned scratch (at most 8 CTAs x 2^11 bins); larger
+// states take the chunked kernel, which accumulates with FP64 atomics
+// straight into the caller's output after zeroing it and needs no scratch
+// (the per-CTA kernel ran 25-30x slower than it on a 30-qubit state on
+// GB300). Every GPU that loads the library keeps these 128 KiB until exit.
 namespace qs {
 std::string &last_error_ref();
 }
 
 namespace {
 
-constexpr int kNoAllocScratchDoubles = 1 << 19;  // 4 MiB
+constexpr int kNoAllocScratchDoubles = 1 << 14;  // 128 KiB
 static __device__ __align__(256) double g_probs_scratch[kNoAllocScratchDoubles];
 
 constexpr int kMaxDevices = 64;
@@ -750,8 +754,8 @@ extern "C" qs_status qs_probs_noalloc(const void *dev_amps, int n, qs_dtype dtyp
   if (dtype != QS_C64 && dtype != QS_C128) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: unknown dtype");
   const int nmax = dtype == QS_C64 ? QS_MAX_N_C64 : QS_MAX_N_C128;
   if (n < 1 || n > nmax) return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: qubit count out of range");
-  if (m < 0 || m > n || m > kProbsSmemBits)
-    return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: m must be in 0..min(n, 12)");
+  if (m < 0 || m > n || m > kMaxProbBits)
+    return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: m must be in 0..min(n, 26)");
   if (((uintptr_t)dev_amps & 15) != 0 || ((uintptr_t)dev_out & 7) != 0)
     return noalloc_fail(QS_EINVAL, "qs_probs_noalloc: misaligned device pointer");
   int pos[kMaxProbBits];
@@ -778,16 +782,24 @@ extern "C" qs_status qs_probs_noalloc(const void *dev_amps, int n, qs_dtype dtyp
     }
     scratch = g_scratch_ptr[dev];
   }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (n >= kProbChunkBits) {
+    // the chunked kernel: zeroes dev_out (an asynchronous memset, no
+    // allocation), then FP64 atomics into it; no scratch
+    e = launch_probs(dev_amps, n, dtype == QS_C128, pos, m, nullptr, dev_out, s);
+    if (e != cudaSuccess) return noalloc_fail(QS_ECUDA, "qs_probs_noalloc: launch failed");
+    return QS_OK;
+  }
   ProbsParam p;
   p.n_amps = 1ll << n;
   p.m = m;
   for (int j = 0; j < m; j++) p.pos[j] = pos[j];
   // every partial slot the reduce kernel reads is written by this call, so
-  // nothing in the array has to start at zero
+  // nothing in the array has to start at zero (at most 8 CTAs x 2^11 bins
+  // below 12 qubits; the cap only guards the array's bounds)
   int grid = probs_grid(n);
   const int cap = kNoAllocScratchDoubles >> m;
   if (grid > cap) grid = cap;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   const size_t smem = sizeof(double) << m;
   if (dtype == QS_C128) k_probs<double2><<<grid, 256, smem, s>>>((const double2 *)dev_amps, p, scratch);
   else k_probs<float2><<<grid, 256, smem, s>>>((const float2 *)dev_amps, p, scratch);

@@ -6,8 +6,9 @@ must not risk the synchronisation cudaMalloc/cudaFree may imply). Its
 scratch is a fixed array inside the library, so the test checks, through the
 C ABI, that two calls in a row give the same marginals as qs_measure_probs
 (which uses state-owned scratch) and as the FP64 oracle, within the
-tolerances of the other probability tests, and that the library's count of
-live device bytes does not move across the calls. The file sorts last so
+tolerances of the other probability tests, on states small enough to use
+the fixed array and on larger ones (no scratch), and that the library's
+count of live device bytes does not move across the calls. The file sorts last so
 that a failure here comes after every other test has run; it also passes on
 its own in a fresh process.
 """
@@ -36,7 +37,7 @@ def test_noalloc_matches_measure_probs_twice(dtype, tol):
                             qs.QS_VSWAP | qs.QS_FUSE | qs.QS_FUSE_K(3) | qs.QS_DIAG)
         perm = qs.qs_get_perm(st, n)
         amps = qs.qs_device_ptr(st)
-        for logical in ([], [0], [3, 17], list(range(12)), [21, 5, 9, 0, 14]):
+        for logical in ([], [0], [3, 17], list(range(12)), [21, 5, 9, 0, 14], list(range(16))):
             want = qs.qs_measure_probs(st, logical)
             phys = [int(perm[l]) for l in logical]
             out = torch.full((1 << len(logical),), -1.0, dtype=torch.float64, device="cuda")
@@ -52,13 +53,15 @@ def test_noalloc_matches_measure_probs_twice(dtype, tol):
         qs.qs_free_state(st)
 
 
+@pytest.mark.parametrize("n", [9, 14])
 @pytest.mark.parametrize("dtype,tol", [(qs.QS_C64, 1e-6), (qs.QS_C128, 1e-13)])
-def test_noalloc_matches_the_oracle(dtype, tol):
-    """Marginals of a 14-qubit layered circuit with SWAPs against the FP64
-    oracle's, twice in a row, the measured bits mapped through perm."""
+def test_noalloc_matches_the_oracle(dtype, tol, n):
+    """Marginals of a layered circuit with SWAPs against the FP64 oracle's,
+    twice in a row, the measured bits mapped through perm: 9 qubits (partial
+    sums in the library's fixed array) and 14 (the chunked kernel, straight
+    into the output)."""
     torch = pytest.importorskip("torch")
     qs.load(build_if_missing=True)
-    n = 14
     gates = cg.random_layered(n, 6, cg.SplitMix64(654), n_swaps=5)
     want_state, _ = oracle.simulate(cg.to_qasm(n, gates))
     st = qs.qs_alloc_state(n, dtype)
@@ -67,7 +70,7 @@ def test_noalloc_matches_the_oracle(dtype, tol):
         perm = qs.qs_get_perm(st, n)
         amps = qs.qs_device_ptr(st)
         torch.cuda.synchronize()
-        for logical in ([13], [2, 11, 7], list(range(12)), list(range(13, 1, -1))):
+        for logical in ([n - 1], [2, n - 3, 7], list(range(min(n, 12))), list(range(n - 1, 1, -1))):
             want = oracle.probs(want_state, logical)
             out = torch.full((1 << len(logical),), -1.0, dtype=torch.float64, device="cuda")
             for _ in range(2):
@@ -79,14 +82,16 @@ def test_noalloc_matches_the_oracle(dtype, tol):
         qs.qs_free_state(st)
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch():
+def test_noalloc_rejects_bad_sizes():
     torch = pytest.importorskip("torch")
     qs.load(build_if_missing=True)
     n = 14
     buf = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
-    out = torch.zeros(1 << 13, dtype=torch.float64, device="cuda")
+    out = torch.zeros(1 << 15, dtype=torch.float64, device="cuda")
     with pytest.raises(qs.QsError) as e:
-        qs.qs_probs_noalloc(buf.data_ptr(), n, qs.QS_C64, list(range(13)), out.data_ptr())
-    assert e.value.status == qs.QS_EINVAL and "12" in str(e.value)
+        qs.qs_probs_noalloc(buf.data_ptr(), n, qs.QS_C64, list(range(15)), out.data_ptr())
+    assert e.value.status == qs.QS_EINVAL and "26" in str(e.value)
     with pytest.raises(qs.QsError):
         qs.qs_probs_noalloc(buf.data_ptr(), n, qs.QS_C64, [1, 1], out.data_ptr())
+    with pytest.raises(qs.QsError):
+        qs.qs_probs_noalloc(buf.data_ptr(), n, qs.QS_C64, [14], out.data_ptr())
