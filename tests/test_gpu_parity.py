@@ -60,18 +60,26 @@ def gpu_run(n, gates, flags, dtype, init=None, logical=False):
         qs.qs_free_state(st)
 
 
+def planned_perm(n, arr, flags, dtype):
+    """The map the host passes predict for these flags (the measured-profile
+    activator of a fresh state has no measurements: its choice is the priors')."""
+    if flags & qs.QS_PGO_MEASURED:
+        flags, _ = qs.qs_pgo_select(n, arr, dtype=dtype)
+    return [int(x) for x in qs.qs_plan(n, arr, flags)[2]]
+
+
 def check(n, gates, flags, dtype, init=None):
     text = cg.to_qasm(n, gates)
     want, operm = oracle.simulate(text, init=init)
-    got, perm = gpu_run(n, qs.gates_to_array(gates), flags, dtype, init=init)
+    arr = qs.gates_to_array(gates)
+    got, perm = gpu_run(n, arr, flags, dtype, init=init)
     pgo = qs.QS_PGO_RULES | qs.QS_PGO_MEASURED | qs.QS_RELOCATE
-    if flags & qs.QS_FOLD and not flags & (qs.QS_VSWAP | pgo):
-        pass  # folding may cancel SWAP pairs; without virtual swap perm stays identity
-    if flags & (qs.QS_VSWAP | pgo) and any(g[0] == "swap" for g in gates):
-        if flags & (qs.QS_PGO_MEASURED | qs.QS_RELOCATE | qs.QS_PGO_RULES):
-            pass  # relocation (or a plan without virtual swap) changes the map
-        else:
-            assert list(perm) == list(operm), (list(perm), list(operm))
+    # bit-exact against the host plan's map under every flag set (relocation
+    # and activator choices included), and against the oracle's composed
+    # SWAP transpositions where only virtual swap relabels
+    assert list(perm) == planned_perm(n, arr, flags, dtype), (list(perm), hex(flags))
+    if flags & qs.QS_VSWAP and not flags & pgo and any(g[0] == "swap" for g in gates):
+        assert list(perm) == list(operm), (list(perm), list(operm))
     elif not flags & (qs.QS_VSWAP | pgo):
         assert list(perm) == list(range(n))
     assert sorted(perm) == list(range(n))
