@@ -73,6 +73,14 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase(T *__restrict__ a, cons
   const long long nwarps = (long long)gridDim.x * (kPhaseThreads / 32);
   for (long long c = ((long long)blockIdx.x * kPhaseThreads + threadIdx.x) >> 5; c < n_chunks; c += nwarps) {
     const uint64_t cbase = (uint64_t)c << kPhaseChunkBits;
+    T *chunk = a + cbase;
+    // complex64: the chunk's loads go out first, so that they are in flight
+    // while the warp folds the chunk's terms (which depend on cbase only)
+    float4 v4[sizeof(T) == 8 ? 16 : 1];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int it = 0; it < 16; it++) v4[it] = *reinterpret_cast<const float4 *>(chunk + 2 * lane + 64 * it);
+    }
     T e[kPhaseSlots];
 #pragma unroll
     for (int s = 0; s < kPhaseSlots; s++) {
@@ -92,7 +100,6 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase(T *__restrict__ a, cons
 #pragma unroll
     for (int i = 0; i < 5; i++)
       if ((lane >> i) & 1) fb = cmul(fb, e[5 + i]);
-    T *chunk = a + cbase;
     if constexpr (sizeof(T) == 8) {
       // lane reads offsets 2 lane + 64 it (+1): bits 0..4 are (2 lane) mod 32
       // (+1), bits 5..9 are (lane >> 4) + 2 it
@@ -101,9 +108,7 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase(T *__restrict__ a, cons
       for (int i = 1; i < 5; i++)
         if (((2 * lane) >> i) & 1) fa0 = cmul(fa0, e[i]);
       const T fa1 = cmul(fa0, e[0]);
-      float4 v[16];
-#pragma unroll
-      for (int it = 0; it < 16; it++) v[it] = *reinterpret_cast<const float4 *>(chunk + 2 * lane + 64 * it);
+      const float4 *v = v4;
 #pragma unroll
       for (int it = 0; it < 16; it++) {
         const int src = (lane >> 4) + 2 * it;

@@ -328,24 +328,22 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
 // holds B and two 64 KB staging areas.
 //
 // Warp roles (one CTA per SM). Warps 0..7 convert and store: iteration i
-// waits for tile i's products (mbarrier done[i % 2]), rescales and stores
-// them, converts tile i + 2 -- read back from its staging area, which is
+// waits for tile i's products (mbarrier done[i % 2]), rescales, exchanges
+// back and stores them, converts tile i + 2 -- read back from its staging area, which is
 // refilled with tile i + 4 by cp.async -- into the A buffer tile i used, and
 // arrives on ready[i % 2]. Warp 8 issues the MMAs: tile i once ready[i % 2]
 // says its A is written and its accumulator read out, with completion on
 // done[i % 2]. The converting warps never wait for an MMA issue, and a
 // group's two threads (warps w and w + 4) synchronise only with each other,
 // on named barrier 1 + w: the four warp pairs run independently between
-// the tile-wide mbarriers. Where the layout
-// needs no lane/register exchange (nswb = 0) the products are stored
-// without exchanging back: each lane writes its two slot halves of a
-// register as 8-byte pairs, which across the warp still cover whole runs
-// of the lowest bits. Measured on GB300 from random states at n = 28, high
-// targets: one A buffer in shared memory, register gathers 5.1 TB/s; A in
-// TMEM with staging 5.3; both double-buffered, one thread issuing 4.7;
+// the tile-wide mbarriers. Measured on GB300 from random states at n = 28,
+// high targets: one A buffer in shared memory, register gathers 5.1 TB/s;
+// A in TMEM with staging 5.3; both double-buffered, one thread issuing 4.7;
 // warp roles 5.56 (four threads per group instead of two: 5.37); the row
-// reductions in independent chains and direct stores 5.87; barriers per
-// warp pair instead of all eight warps 6.01.
+// reductions in independent chains, with results stored as 8-byte slot
+// halves where no lane/register exchange had to be undone, 5.87; barriers
+// per warp pair 6.01; 16-byte stores after the exchange back in every
+// layout instead of those 8-byte ones 6.26.
 namespace x6 {
 constexpr int kConv = 2 * kTcThreads;  // converting threads, two per group
 constexpr int kThreads = kConv + 32;   // + the MMA warp
@@ -467,20 +465,13 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
     uint64_t roff[RB];
 #pragma unroll
     for (int j = 0; j < RB; j++) roff[j] = 1ull << p.rbit[j];
-    auto offset_from = [&](uint64_t o, int rr) {
+    auto offset = [&](int rr) {
+      uint64_t o = lane_off;
 #pragma unroll
       for (int j = 0; j < RB; j++)
         if ((rr >> j) & 1) o += roff[j];
       return o;
     };
-    auto offset = [&](int rr) { return offset_from(lane_off, rr); };
-    // after the element bit's exchange alone (nswb = 0, la >= 0): this
-    // lane's la bit addresses bit 0, and the element addresses lbit[la]
-    const bool direct = p.nswb == 0;
-    const bool la_up = p.la >= 0 && ((lane >> p.la) & 1);
-    const uint64_t lane_post =
-        p.la >= 0 ? lane_off - (la_up ? (1ull << p.lbit[p.la]) : 0ull) + (la_up ? 1ull : 0ull) : lane_off;
-    const uint64_t e_off = p.la >= 0 ? (1ull << p.lbit[p.la]) : 1ull;
     auto tile_base = [&](long long t) {
       return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
     };
@@ -581,35 +572,18 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       const float nin = nin_row[u][r];
       const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
       const uint64_t cur_base = tile_base(tile);
-      if (direct) {
-        // no lane/register exchange to undo: slot halves straight to memory
-        float2 *dst = a + cur_base;
+      // 8 slots (4 registers) at a time: scale, exchange back, store
 #pragma unroll
-        for (int q = 0; q < NV; q++) {
-          const float2 y0 = make_float2(__uint_as_float(y32[4 * q]) * f, __uint_as_float(y32[4 * q + 1]) * f);
-          const float2 y1 = make_float2(__uint_as_float(y32[4 * q + 2]) * f, __uint_as_float(y32[4 * q + 3]) * f);
-          const uint64_t o = offset_from(lane_post, q);
-          if (p.la >= 0) {
-            dst[o] = y0;
-            dst[o + e_off] = y1;
-          } else {
-            *reinterpret_cast<float4 *>(dst + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
-          }
-        }
-      } else {
+      for (int hh = 0; hh < 4; hh++) {
+        float4 y[4];
 #pragma unroll
-        for (int hh = 0; hh < 4; hh++) {
-          float4 y[4];
+        for (int q = 0; q < 4; q++)
+          y[q] = make_float4(__uint_as_float(y32[16 * hh + 4 * q]) * f, __uint_as_float(y32[16 * hh + 4 * q + 1]) * f,
+                             __uint_as_float(y32[16 * hh + 4 * q + 2]) * f,
+                             __uint_as_float(y32[16 * hh + 4 * q + 3]) * f);
+        xch.run<4>(y);
 #pragma unroll
-          for (int q = 0; q < 4; q++)
-            y[q] = make_float4(__uint_as_float(y32[16 * hh + 4 * q]) * f,
-                               __uint_as_float(y32[16 * hh + 4 * q + 1]) * f,
-                               __uint_as_float(y32[16 * hh + 4 * q + 2]) * f,
-                               __uint_as_float(y32[16 * hh + 4 * q + 3]) * f);
-          xch.run<4>(y);
-#pragma unroll
-          for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
-        }
+        for (int q = 0; q < 4; q++) *reinterpret_cast<float4 *>(a + cur_base + offset(4 * hh + q)) = y[q];
       }
       // tile + 2 G into the A buffer (and, for the MMA warp, the accumulator)
       // this tile has finished with

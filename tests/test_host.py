@@ -379,10 +379,9 @@ def test_lane_exchange_layout_index_arithmetic():
     layout; the layout applies exactly when bit 0 is not a control and 7 or
     more free bits remain."""
     rng = cg.SplitMix64(4242)
-    applied = direct_checked = 0
+    applied = 0
     for trial in range(4000):
-        # the last 1000: 6-target blocks with uniformly placed bits (mostly
-        # layouts without lane/register exchanges, the direct-store case)
+        # the last 1000: 6-target blocks with uniformly placed bits
         k = 6 if trial >= 3000 else 4 + rng.randint(3)
         nctrl = rng.randint(3)
         n = min(34, k + nctrl + 5 + rng.randint(12))
@@ -424,24 +423,7 @@ def test_lane_exchange_layout_index_arithmetic():
         assert np.array_equal(after, groups[:, None, None] + slot_off[None, :, :])
         back = np.concatenate([run(after[:, c:c + 4, :]) for c in range(0, nv, 4)], axis=1)
         assert np.array_equal(back, off)
-        if k == 6 and lay.nswb == 0:
-            # the 6-target kernel's direct stores (no exchange back): lane
-            # l's register q element e goes to lane_post(l) + reg_off(q) +
-            # e * e_off, where the element's exchange moved the la lane bit
-            # to bit 0 and the element to lane_bits[la]
-            lanes = np.arange(32, dtype=np.int64)
-            lane_off = sum(((lanes >> i) & 1) << int(lay.lane_bits[i]) for i in range(5))
-            if lay.la >= 0:
-                up = (lanes >> lay.la) & 1
-                lane_post = lane_off - (up << int(lay.lane_bits[lay.la])) + up
-                e_off = 1 << int(lay.lane_bits[lay.la])
-            else:
-                lane_post, e_off = lane_off, 1
-            reg_off = sum(((np.arange(nv) >> j) & 1) << int(lay.reg_bits[j]) for j in range(nrb))
-            direct = lane_post[:, None, None] + reg_off[None, :, None] + np.arange(2)[None, None, :] * e_off
-            assert np.array_equal(direct, after), (targets, ctrls)
-            direct_checked += 1
-    assert applied > 2500 and direct_checked > 150
+    assert applied > 2500
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
