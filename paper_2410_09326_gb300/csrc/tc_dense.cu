@@ -207,7 +207,12 @@ __global__ void __launch_bounds__(kTcThreads, TcOcc<K>::value)
     float nin_cur = 0.f;
     if (RENORM) {
 #pragma unroll
-      for (int s = 0; s < D; s++) nin_cur = fmaf(v[s].x, v[s].x, fmaf(v[s].y, v[s].y, nin_cur));
+      {
+        // squared norm in four independent chains
+        float s4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int s = 0; s < D; s++) s4[s & 3] = fmaf(v[s].x, v[s].x, fmaf(v[s].y, v[s].y, s4[s & 3]));
+        nin_cur = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      }
     }
     gather(tile + gridDim.x, base, valid);  // next tile, in flight during the MMAs
     const bool ok = mbar_wait(mbar_a, phase);
@@ -240,9 +245,10 @@ __global__ void __launch_bounds__(kTcThreads, TcOcc<K>::value)
       // the computed group to its input norm removes the shrinkage left by
       // the tensor core's round-toward-zero accumulation.
       const float nin = nin_cur;
-      float nout = 0.f;
+      float o4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int i = 0; i < KR; i++) nout = fmaf(__uint_as_float(r[i]), __uint_as_float(r[i]), nout);
+      for (int i = 0; i < KR; i++) o4[i & 3] = fmaf(__uint_as_float(r[i]), __uint_as_float(r[i]), o4[i & 3]);
+      const float nout = (o4[0] + o4[1]) + (o4[2] + o4[3]);
       const float f = nout > 0.f ? sqrtf(nin / nout) : 1.f;
 #pragma unroll
       for (int i = 0; i < KR; i++) r[i] = __float_as_uint(__uint_as_float(r[i]) * f);

@@ -201,6 +201,32 @@ def test_tc_steady_state_loop(k, exchange, max_ctas):
         assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl)
 
 
+@pytest.mark.parametrize("max_ctas", [0, 3])
+@pytest.mark.parametrize("k", [4, 5])
+def test_tc_tf32_operands(k, max_ctas):
+    """The 3 x TF32 tensor-core kernel (opts.tc_precision = 1, the precision
+    option beside the default FP16 halves): high, low, bit-0 and mixed
+    targets, with and without a control, one wave of CTAs or 3 CTAs looping
+    over the tiles, n = 17 from a random state, against the oracle."""
+    n = 17
+    rng = cg.SplitMix64(6100 + 10 * k + max_ctas)
+    init = random_state(n, rng)
+    o = qs.qs_default_opts()
+    o.tc_precision = 1
+    o.tc_max_ctas = max_ctas
+    for pattern, ctrl in (([12, 13, 14, 15, 16], None), ([0, 1, 2, 3, 4], None), ([1, 2, 8, 9, 10], None),
+                          ([0, 5, 9, 13, 15], 16)):
+        qubits = sorted(pattern[:k])
+        gates = block_gates(qubits, rng, ctrl)
+        want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+        got, recs = run_tc_block(n, gates, k + (0 if ctrl is None else 1), init, o)
+        blk = [r for r in recs if r.kind == 0 and r.k == k]
+        assert len(blk) == 1 and blk[0].tc == 1, (qubits, ctrl)
+        if max_ctas:
+            assert blk[0].ctas <= max_ctas and blk[0].tiles >= 3 * blk[0].ctas
+        assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl)
+
+
 @pytest.mark.parametrize("max_ctas", [0, 4])
 @pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("k,ctrl", [(4, None), (4, 5), (4, 0), (5, None), (5, 5), (5, 0), (6, None)])
@@ -496,13 +522,15 @@ def test_errors_leave_state_usable():
     assert e.value.status == qs.QS_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("k,exchange", [(4, 1), (4, 2), (5, 0), (5, 1), (6, 2), (6, 1)])
-def test_bounded_wait_times_out_and_state_recovers(k, exchange):
+@pytest.mark.parametrize("k,exchange,precision", [(4, 1, 0), (4, 2, 0), (5, 0, 0), (5, 1, 0), (6, 2, 0), (6, 1, 0),
+                                                   (5, 0, 1)])
+def test_bounded_wait_times_out_and_state_recovers(k, exchange, precision):
     """Failure detection without a GPU fault: the test hook withholds the
     tensor cores' completion signal, the kernel's 1 s wait runs out, the CTA
     frees its TMEM and returns, and the next synchronising call reports
     QS_ETIMEOUT. The state stays usable. Lane-exchange kernels (4, 5 targets
-    staged by cp.async, 6 targets) and the thread-per-group ones."""
+    staged by cp.async, 6 targets), the thread-per-group ones and the 3 x TF32
+    one."""
     n = 14
     gates = [("u3", [q], [0.1 * q, 0.2, 0.3]) for q in range(k)] + [("cx", [q, q + 1]) for q in range(0, k - 1, 2)]
     gates += [("cx", [k - 2, k - 1])]
@@ -512,9 +540,10 @@ def test_bounded_wait_times_out_and_state_recovers(k, exchange):
         opts = qs.qs_default_opts()
         opts.test_wait_timeout = 1
         opts.tc_exchange = exchange
+        opts.tc_precision = precision
         qs.qs_apply_circuit(st, arr, qs.QS_FUSE | qs.QS_FUSE_K(k) | qs.QS_TC, opts)
         _, recs = qs.qs_profile(st)
-        assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [1 if exchange == 1 else 2]
+        assert [r.tc for r in recs if r.kind == 0 and r.k == k] == [1 if exchange == 1 or precision else 2]
         with pytest.raises(qs.QsError) as e:
             qs.qs_norm(st)
         assert e.value.status == qs.QS_ETIMEOUT
