@@ -698,7 +698,7 @@ def run_costmodel_bench(args):
     from paper_2410_09326_gb300 import costmodel
     qs.load(build_if_missing=True)
     t0 = time.perf_counter()
-    train = costmodel.training_circuits(args.train_circuits, n_lo=20, n_hi=28, index0=1000)
+    train = costmodel.training_circuits(args.train_circuits, n_lo=args.train_n_lo, n_hi=args.train_n_hi, index0=1000)
     x, y = costmodel.build_dataset(train)
     t_data = time.perf_counter() - t0
     m = qs.qs_mlp_create(7)
@@ -736,7 +736,8 @@ def run_costmodel_bench(args):
         out[name] = res
     qs.qs_mlp_free(m)
     torch.cuda.synchronize()
-    line = {"config": "costmodel", "workload": f"train: {len(train)} seeded circuits n=20..28 (random layered, "
+    line = {"config": "costmodel", "workload": f"train: {len(train)} seeded circuits "
+                                                f"n={args.train_n_lo}..{args.train_n_hi} (random layered, "
                                                 f"QFT, GHZ, QAOA) x {len(costmodel.TRAIN_FLAGS)} flag sets; test: "
                                                 "unseen n=30 GHZ / QFT / random",
             "samples": int(len(y)), "profiling_s": round(t_data, 1), "train_s": round(t_train, 2),
@@ -901,6 +902,8 @@ def main():
     ap.add_argument("--config", default="main", choices=["main", "batch", "costmodel", "tc32", "ablation", "oracle"],
                     help="batch: 512-circuit persistent launch; costmodel: learned activator (own JSON lines)")
     ap.add_argument("--train-circuits", type=int, default=60)
+    ap.add_argument("--train-n-lo", type=int, default=20, help="costmodel: narrowest training circuit")
+    ap.add_argument("--train-n-hi", type=int, default=28, help="costmodel: widest training circuit")
     ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--qft-max", type=int, default=32, help="ablation: widest QFT of the virtual-swap table")
     ap.add_argument("--oracle-target-s", type=float, default=3.0, help="oracle: seconds of gates timed per sample")
