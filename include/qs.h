@@ -130,9 +130,10 @@ typedef struct {
                            blocks with one or more); 1 = never; 2 = wherever the layout allows
                            (bit 0 not a control, whole tiles of 128 groups) */
   int tc_max_ctas;      /* test hook, 0 in normal use: at most this many CTAs per tensor-core
-                           launch (normally one wave of resident CTAs, no more than there are
-                           tiles), so that every CTA loops over several tiles even on a small
-                           state; the block records report tiles and CTAs */
+                           or phase-polynomial launch (normally one wave of resident CTAs, no
+                           more than there are tiles or chunks), so that every CTA loops over
+                           several tiles (every warp over several 1024-amplitude chunks) even
+                           on a small state; the block records report tiles (chunks) and CTAs */
   int n_global;         /* sharding tier (qs_plan only; 0 elsewhere): the top n_global physical
                            bits are global -- a state sharded over 2^n_global ranks, one shard per
                            value of those bits (Sec. II-B's file segment, across ranks). The plan
@@ -241,9 +242,10 @@ typedef struct {
   double bytes;      /* algorithmic bytes: 2 x amplitudes changed x amplitude size */
   double t_start_ms; /* start relative to the first block (QS_PROFILE), else -1 */
   double ms;         /* device time (QS_PROFILE), else -1 */
-  int64_t tiles;     /* tensor-core blocks of an apply call: tiles of 128 groups; else 0 */
-  int32_t ctas;      /* tensor-core blocks of an apply call: CTAs launched (each loops over
-                        tiles ctas apart); else 0 */
+  int64_t tiles;     /* blocks of an apply call: tensor-core blocks, tiles of 128 groups;
+                        phase polynomials, chunks of 1024 amplitudes; else 0 */
+  int32_t ctas;      /* the same blocks: CTAs launched (each loops over tiles ctas apart;
+                        each of a phase CTA's 8 warps over chunks 8 ctas apart); else 0 */
   int32_t reserved;
 } qs_block_record;
 

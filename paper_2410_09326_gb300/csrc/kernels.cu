@@ -396,7 +396,7 @@ cudaError_t launch_block_with_matrix(void *amps, int n, bool c128, const Block &
                                      int *err, cudaStream_t s, int threads, LaunchShape *shape) {
   if (threads <= 0) threads = 256;
   if (b.kind == BK_TILE) return run_tile(amps, n, c128, b, dev_mat, s);
-  if (b.kind == BK_PHASE) return run_phase(amps, n, c128, b, dev_mat, s);
+  if (b.kind == BK_PHASE) return run_phase(amps, n, c128, b, dev_mat, s, shape);
   if (b.kind == BK_DENSE && b.tc && !c128)
     return b.tc_tf32 ? run_dense_tc((float2 *)amps, n, b, dev_mat, err, s, shape)
                      : run_dense_tc16((float2 *)amps, n, b, dev_mat, err, s, shape);

@@ -224,7 +224,8 @@ cudaError_t run_tile(void *a, int n, bool c128, const Block &b, const void *dev_
 // chunk terms in device memory.
 size_t phase_desc_bytes(const Block &b, bool c128);
 void phase_fill_desc(const Block &b, bool c128, void *out);
-cudaError_t run_phase(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s);
+cudaError_t run_phase(void *a, int n, bool c128, const Block &b, const void *dev_desc, cudaStream_t s,
+                      LaunchShape *shape);
 
 // Warp-shuffle variant for 1..3 targets with one among bits 1..5 (dense_shfl.cu);
 // used = false when the block does not qualify (nothing launched).

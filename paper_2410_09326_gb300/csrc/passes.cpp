@@ -930,7 +930,7 @@ qs_status build_plan(int n, const qs_gate *gates, size_t n_gates, uint64_t flags
     b.tc_xg = b.tc && !tf32 && opts.tc_exchange != 1 && (opts.tc_exchange == 2 || tc_exchange_pays(b)) &&
               tc_exchange_layout(n, b, xl);
     b.withhold_commit = b.tc && opts.test_wait_timeout != 0;
-    b.tc_max_ctas = b.tc ? opts.tc_max_ctas : 0;
+    b.tc_max_ctas = (b.tc || b.kind == BK_PHASE) ? opts.tc_max_ctas : 0;
   }
   return QS_OK;
 }

@@ -64,7 +64,7 @@ struct Block {
   bool shuffles = true;           // CUDA-core blocks with low targets: warp-shuffle kernel
   bool tc_xg = false;             // 4..6-target tensor-core blocks: lane-exchange gathers (tc16x.cu)
   bool withhold_commit = false;   // test hook (qs_opts.test_wait_timeout)
-  int tc_max_ctas = 0;            // test hook (qs_opts.tc_max_ctas): cap on tensor-core CTAs
+  int tc_max_ctas = 0;            // test hook (qs_opts.tc_max_ctas): cap on tensor-core and phase CTAs
   // tile pass (BK_TILE): k = tile qubits, tile_q their physical positions
   // ascending (0..kTileLowBits-1 first); sub = the member blocks in order,
   // dense targets inside the tile, diagonal qubits and controls anywhere

@@ -43,6 +43,7 @@ struct TcXParam {
   int nswb;                   // lane bits lb[i] exchanged with register bits i
   int lb[2];
   int part_bit[2];            // 6 targets: the target bits thread part h fixes (bit j of h -> part_bit[j])
+  int stage_xch;              // 1: the lane/register exchanges of the loads in the staging copies
   int withhold_commit;
 };
 
@@ -59,6 +60,10 @@ struct LaneExchange {
   __device__ __forceinline__ LaneExchange(const TcXParam &p, int lane_)
       : la(p.la), nswb(p.nswb), lb0(p.lb[0]), lb1(p.lb[1]), lane(lane_) {}
   template <int N> __device__ __forceinline__ void run(float4 *w) const {
+    element<N>(w);
+    lanes<N>(w);
+  }
+  template <int N> __device__ __forceinline__ void element(float4 *w) const {
     if (la >= 0) {
       const bool up = (lane >> la) & 1;
       const unsigned m = 1u << la;
@@ -75,6 +80,8 @@ struct LaneExchange {
         }
       }
     }
+  }
+  template <int N> __device__ __forceinline__ void lanes(float4 *w) const {
 #pragma unroll
     for (int i = 0; i < 2; i++) {
       if (i >= nswb) break;
@@ -98,13 +105,49 @@ struct LaneExchange {
 };
 
 // The loads go to shared memory by cp.async, two tiles ahead (two staging
-// areas); each thread copies and later reads back exactly its own 16-byte
-// chunks (consecutive threads, consecutive chunks), so no barrier guards the
-// staging areas. Without registers held for tiles in flight the SM keeps four
+// areas, [register][thread] 16-byte slots); each thread reads back its own
+// slots, which lanes of its own warp filled (staging_slots below), so a
+// __syncwarp is all that guards an area. Without registers held for tiles in flight the SM keeps four
 // tiles (128 KB at 5 targets) on the way: the n = 30 benchmark step's
 // dominant kernel went from 5.95 (one tile ahead in registers) to 6.36 TB/s
 // on GB300. Resident CTAs per SM: 4 (K = 4), 2 (K = 5).
 template <int K> constexpr int tc16x_occ() { return K <= 4 ? 4 : 2; }
+
+// With p.stage_xch the lane/register exchanges of the loads happen in the
+// staging copies: after them, lane L's register q holds what the load layout puts at lane L
+// with bit lb[i] set to bit i of q and register q with bit i set to bit
+// lb[i] of L (both i < nswb), so the copy of load-layout register q goes
+// straight to the staging row of the register that holds it after the
+// exchange. Only register bits 0 and 1 take part. Within row r the slots
+// are swizzled: lane L's slot is L ^ S(r), S(r) = sum_i (bit i of r) << lb[i],
+// which keeps both the copies of one instruction and the read-back of one
+// row free of bank conflicts (without it, copies whose lanes differ only in
+// bits lb[i] < 3 hit one bank group: the 5-target kernel fell to 4.0 TB/s
+// with targets 0..4). wdst[q & 3] + (q & ~3) * stride is where this lane's
+// copy of register q goes, rdst[r & 3] + (r & ~3) * stride the slot it
+// reads for register r. Threads read chunks other lanes of their warp
+// copied, so a __syncwarp follows the wait for the copies (and precedes a
+// refill of the area). Measured on GB300 (n = 28, random states) against
+// the shuffles: 6 to 12% faster with lb[i] >= 1 (the copies of one 32-byte
+// sector stay together), but 6 to 22% slower where lane bit 0 takes part
+// (each sector split over two rows), so the host sets stage_xch only where
+// every lb[i] >= 1 and the shuffles do the exchanges elsewhere.
+__device__ __forceinline__ void staging_slots(const TcXParam &p, int warp, int lane, uint32_t stride,
+                                              uint32_t wdst[4], uint32_t rdst[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; c++) {
+    int rl = c, sw = 0;
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      if (!p.stage_xch || i >= p.nswb) break;
+      const int lb = p.lb[i];
+      rl = (rl & ~(1 << i)) | (((lane >> lb) & 1) << i);
+      sw |= ((c >> i) & 1) << lb;
+    }
+    wdst[c] = (uint32_t)rl * stride + (uint32_t)(warp * 32 + (lane ^ sw)) * 16u;
+    rdst[c] = (uint32_t)c * stride + (uint32_t)(warp * 32 + (lane ^ sw)) * 16u;
+  }
+}
 
 template <int K>
 __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
@@ -167,6 +210,8 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     return o;
   };
   const LaneExchange xch(p, lane);
+  uint32_t wdst[4], rdst[4];
+  staging_slots(p, warp, lane, kTcThreads * 16u, wdst, rdst);
 
   uint32_t phase = 0;
   bool aborted = false;
@@ -188,9 +233,10 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
       svalid0 = ok;
     }
     if (ok) {
-      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+      const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-      for (int r = 0; r < NV; r++) cp_async16(dst + (uint32_t)r * kTcThreads * 16u, a + b + offset(r));
+      for (int r = 0; r < NV; r++)
+        cp_async16(dst + (uint32_t)(r & ~3) * kTcThreads * 16u + wdst[r & 3], a + b + offset(r));
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -201,14 +247,17 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     {
       // this tile's group has landed once at most the next one is pending
       asm volatile("cp.async.wait_group 1;" ::: "memory");
+      if (p.stage_xch) __syncwarp();
       const int u = it & 1;
-      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-      for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)r * kTcThreads * 16u);
+      for (int r = 0; r < NV; r++)
+        v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)(r & ~3) * kTcThreads * 16u + rdst[r & 3]);
       base = u ? sbase1 : sbase0;
       valid = u ? svalid1 : svalid0;
     }
-    xch.run<NV>(v);
+    if (p.stage_xch) xch.element<NV>(v);
+    else xch.run<NV>(v);
     // row max and squared norm in four independent chains
     float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -476,15 +525,17 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
     };
     const LaneExchange xch(p, lane);
+    uint32_t wdst[4], rdst[4];
+    staging_slots(p, warp, lane, NT * 16u, wdst, rdst);
 
     // tile t into staging area u: this thread's 16 chunks, one commit group
     // per tile (empty past the last tile, so the group count stays uniform)
     auto stage_in = [&](long long t, int u) {
       if (t < p.n_tiles) {
         const uint64_t b = tile_base(t);
-        const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+        const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-        for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)q * NT * 16u, a + b + offset(q));
+        for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)(q & ~3) * NT * 16u + wdst[q & 3], a + b + offset(q));
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -493,13 +544,18 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
     // input norm (both halves) goes to nin_row[u]; then arrives on ready[u]
     auto convert = [&](long long t, int u) {
       asm volatile("cp.async.wait_group 1;" ::: "memory");
+      if (p.stage_xch) __syncwarp();
       float4 v[NV];
-      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES + (uint32_t)tid * 16u;
+      const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-      for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)q * NT * 16u);
-      xch.run<NV>(v);
-      // the shuffles consumed the values read back: refill this thread's own
-      // chunks of the area with tile t + 2 G
+      for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)(q & ~3) * NT * 16u + rdst[q & 3]);
+      if (p.stage_xch) {
+        xch.element<NV>(v);
+        __syncwarp();  // every lane of the warp has read its slots
+      } else {
+        xch.run<NV>(v);
+      }
+      // refill the area with tile t + 2 G
       stage_in(t + 2 * G, u);
       // row max and squared norm in four independent chains
       float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
@@ -606,7 +662,11 @@ void fill_xparam(int K, int n, const Block &b, const TcXLayout &x, TcXParam &p) 
   for (int j = 0; j < (K == 6 ? 4 : K - 1); j++) p.rbit[j] = x.rbit[j];
   p.la = x.la;
   p.nswb = x.nswb;
-  for (int i = 0; i < x.nswb; i++) p.lb[i] = x.lb[i];
+  p.stage_xch = x.nswb > 0;
+  for (int i = 0; i < x.nswb; i++) {
+    p.lb[i] = x.lb[i];
+    if (x.lb[i] < 1) p.stage_xch = 0;  // lane bit 0 takes part: shuffles (see staging_slots)
+  }
   p.part_bit[0] = x.part_bit[0];
   p.part_bit[1] = x.part_bit[1];
   p.withhold_commit = b.withhold_commit ? 1 : 0;

@@ -287,6 +287,15 @@ def test_tc_lane_exchange(n, k, ctrl, mode, max_ctas):
         assert np.linalg.norm(got - want) <= 1e-5, (qubits, ctrl, mode)
     if mode == 2 and ctrl != 0 and n == 17:
         assert 2 in kinds
+    if k == 5 and ctrl is None:
+        # both ways of doing the lane/register exchanges run above: in the
+        # staging copies (every exchanged lane bit >= 1) and by shuffles
+        lbs = []
+        for pattern in patterns:
+            x = qs.qs_tc_exchange_layout(n, pattern)
+            if x.applies and x.nswb:
+                lbs.append(min(int(x.lb[i]) for i in range(x.nswb)))
+        assert any(b >= 1 for b in lbs) and any(b == 0 for b in lbs), lbs
 
 
 @pytest.mark.parametrize("shuffles", [0, 1])

@@ -97,3 +97,32 @@ def test_qft_closed_form_n22():
         phys |= ((ys >> l) & 1) << int(perm[l])
     want = np.exp(2j * np.pi * ((x * ys) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
     assert np.linalg.norm(psi[phys] - want) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", [qs.QS_C64, qs.QS_C128])
+@pytest.mark.parametrize("ctas", [1, 3])
+def test_several_chunks_per_warp(dtype, ctas):
+    """The phase kernel's chunk loop (complex64: the next chunk staged in
+    shared memory while the current one is applied) over many chunks per
+    warp: the launch capped to 1 or 3 CTAs of 8 warps on n = 17 (128
+    chunks), against the oracle."""
+    n = 17
+    gates = diagonal_circuit(n, 300, 7200 + ctas)
+    init = random_state(n, 11 + ctas)
+    want, _ = oracle.simulate(cg.to_qasm(n, gates), init=init)
+    o = qs.qs_default_opts()
+    o.tc_max_ctas = ctas
+    st = qs.qs_alloc_state(n, dtype)
+    try:
+        qs.qs_write_state(st, init.astype(np.complex64 if dtype == qs.QS_C64 else np.complex128))
+        qs.qs_apply_circuit(st, qs.gates_to_array(gates), FLAGS, opts=o)
+        _, recs = qs.qs_profile(st)
+        perm = qs.qs_get_perm(st, n)
+        got = qs.qs_read_state(st, n, dtype).astype(np.complex128)
+    finally:
+        qs.qs_free_state(st)
+    ph = [r for r in recs if r.kind == 4]
+    assert ph and all(r.ctas == ctas and r.tiles == 1 << (n - 10) for r in ph)
+    assert all(r.tiles >= 3 * 8 * r.ctas for r in ph)  # several chunks per warp
+    err = np.linalg.norm(got - oracle.to_physical(want, perm))
+    assert err <= TOL[dtype], err
