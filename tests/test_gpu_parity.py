@@ -237,8 +237,9 @@ def test_tc_lane_exchange(n, k, ctrl, mode, max_ctas):
     (opts.tc_exchange: 0 automatic, 1 never, 2 wherever the layout allows)
     on low-bit target patterns (no exchange, the element bit's exchange, one
     or two lane/register exchanges, targets moved from lane to register bits
-    to keep two), without a control, with a control on bit 5 and with bit 0
-    a control (no exchange layout), one tile (n = 12) and many (n = 17), one
+    to keep two or because they lie past the first 128-byte run), without a
+    control, with a control on bit 5 and with bit 0 a control (no exchange
+    layout), one tile (n = 12) and many (n = 17), one
     wave of CTAs or at most 4 CTAs looping over the tiles, from a random
     state; the record's tc field says which kernel ran (2 = lane exchange)."""
     rng = cg.SplitMix64(1300 + 10 * k + n + (ctrl or 0))
@@ -249,7 +250,7 @@ def test_tc_lane_exchange(n, k, ctrl, mode, max_ctas):
     init /= np.linalg.norm(init)
     patterns = ([7, 8, 9, 10, 11], [1, 7, 8, 9, 10], [2, 7, 8, 9, 10], [3, 7, 8, 9, 10], [0, 7, 8, 9, 10],
                 [0, 1, 8, 9, 10], [1, 2, 8, 9, 10], [2, 3, 8, 9, 10], [1, 2, 3, 9, 10], [0, 1, 2, 3, 9],
-                [0, 1, 2, 3, 4], [1, 2, 3, 4, 5])
+                [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], [1, 4, 9, 10, 11], [0, 2, 5, 9, 10])
     kinds = set()
     for pattern in patterns:
         # 6 targets: the pattern plus the lowest qubit above it

@@ -376,8 +376,9 @@ def test_lane_exchange_layout_index_arithmetic():
     exchanges every lane holds one group -- one assignment of the free bits
     -- in slot order (slot bit s -> target slot_target[s]); the exchanges run
     again 4 registers at a time (as the kernels' stores do) restore the load
-    layout; the layout applies exactly when bit 0 is not a control and 7 or
-    more free bits remain."""
+    layout; no target but the element bit's partner sits on a lane bit
+    above bit 3; the layout applies exactly when bit 0 is not a control and
+    7 or more free bits remain."""
     rng = cg.SplitMix64(4242)
     applied = 0
     for trial in range(4000):
@@ -409,6 +410,11 @@ def test_lane_exchange_layout_index_arithmetic():
         else:
             assert list(lay.part_bits) == [-1, -1]
         assert 0 <= lay.nswb <= 2
+        # loads read whole 128-byte lines where they can: no target sits on
+        # a lane bit above bit 3 but the element bit's partner
+        lane_t = [b for b in lay.lane_bits if b in inner]
+        partner = [] if 0 in inner else [min(lane_t)]
+        assert all(b <= 3 for b in lane_t if b not in partner), (targets, list(lay.lane_bits))
         off, run = exchange_emulation(lay, k)
         after = run(off)
         tmask = sum(1 << t for t in inner)
