@@ -83,17 +83,30 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase(T *__restrict__ a, cons
 #pragma unroll
       for (int it = 0; it < 16; it++) v4[it] = *reinterpret_cast<const float4 *>(chunk + 2 * lane + 64 * it);
     }
+    // the warp folds the terms together: lane l takes terms l, l + 32, ...
+    // of each slot, then a butterfly over the lanes multiplies the partial
+    // products (every lane ends with the whole product)
     T e[kPhaseSlots];
 #pragma unroll
     for (int s = 0; s < kPhaseSlots; s++) {
       T acc;
       acc.x = 1;
       acc.y = 0;
-      for (int t = off[s]; t < off[s + 1]; t++) {
+      for (int t = off[s] + lane; t < off[s + 1]; t += 32) {
         const unsigned long long mk = terms[t].mask;
         if ((cbase & mk) == mk) acc = cmul(acc, terms[t].f);
       }
       e[s] = acc;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+#pragma unroll
+      for (int s = 0; s < kPhaseSlots; s++) {
+        T o;
+        o.x = __shfl_xor_sync(0xffffffffu, e[s].x, d);
+        o.y = __shfl_xor_sync(0xffffffffu, e[s].y, d);
+        e[s] = cmul(e[s], o);
+      }
     }
     // second factor: lane l holds the one for bits 5..9 equal to l
     T fb;
