@@ -2,7 +2,9 @@
 // halves, as in tc16.cu) with lane-exchange gathers: a warp loads the
 // sub-cube spanned by a block's targets and its five lowest free bits in
 // address order and exchanges bits between lanes, registers and the 16-byte
-// element with warp shuffles until each lane holds one whole group; B is built
+// element (warp shuffles; lane/register exchanges of the loads, where lane
+// bit 0 takes no part, by the staging copies' placement) until each lane
+// holds one whole group; B is built
 // in the same "slot" order (tc16_build_b). The host layout (which bits sit on
 // lanes and registers, which exchanges run) is tc_exchange_layout below; the
 // planner picks these kernels where tc_exchange_pays.
