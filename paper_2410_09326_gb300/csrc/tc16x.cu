@@ -45,7 +45,7 @@ struct TcXParam {
   int nswb;                   // lane bits lb[i] exchanged with register bits i
   int lb[2];
   int part_bit[2];            // 6 targets: the target bits thread part h fixes (bit j of h -> part_bit[j])
-  int stage_xch;              // 1: the lane/register exchanges of the loads in the staging copies
+  int stage_xch;              // bit i: lane/register exchange i of the loads done by the staging copies
   int withhold_commit;
 };
 
@@ -83,10 +83,12 @@ struct LaneExchange {
       }
     }
   }
-  template <int N> __device__ __forceinline__ void lanes(float4 *w) const {
+  // the lane/register exchanges, but for those in skip (bit i: exchange i)
+  template <int N> __device__ __forceinline__ void lanes(float4 *w, int skip = 0) const {
 #pragma unroll
     for (int i = 0; i < 2; i++) {
       if (i >= nswb) break;
+      if ((skip >> i) & 1) continue;
       const int lbi = i == 0 ? lb0 : lb1;
       const bool up = (lane >> lbi) & 1;
 #pragma unroll
@@ -115,10 +117,10 @@ struct LaneExchange {
 // on GB300. Resident CTAs per SM: 4 (K = 4), 2 (K = 5).
 template <int K> constexpr int tc16x_occ() { return K <= 4 ? 4 : 2; }
 
-// With p.stage_xch the lane/register exchanges of the loads happen in the
-// staging copies: after them, lane L's register q holds what the load layout puts at lane L
-// with bit lb[i] set to bit i of q and register q with bit i set to bit
-// lb[i] of L (both i < nswb), so the copy of load-layout register q goes
+// The lane/register exchanges i of the loads with bit i of p.stage_xch set
+// happen in the staging copies: after them, lane L's register q holds what
+// the load layout puts at lane L with bit lb[i] set to bit i of q and
+// register q with bit i set to bit lb[i] of L, so the copy of load-layout register q goes
 // straight to the staging row of the register that holds it after the
 // exchange. Only register bits 0 and 1 take part. Within row r the slots
 // are swizzled: lane L's slot is L ^ S(r), S(r) = sum_i (bit i of r) << lb[i],
@@ -132,8 +134,13 @@ template <int K> constexpr int tc16x_occ() { return K <= 4 ? 4 : 2; }
 // refill of the area). Measured on GB300 (n = 28, random states) against
 // the shuffles: 6 to 12% faster with lb[i] >= 1 (the copies of one 32-byte
 // sector stay together), but 6 to 22% slower where lane bit 0 takes part
-// (each sector split over two rows), so the host sets stage_xch only where
-// every lb[i] >= 1 and the shuffles do the exchanges elsewhere.
+// (each sector split over two rows), and slower too where a load's runs are
+// shorter than 256 bytes and the staged pieces shorter than 64 bytes
+// (targets 1, 2, 3, 4, 20: 4993 -> 4710 GB/s; 0, 1, 2, 3, 4 with lane bit
+// 0's exchange left to the shuffles: 5225 -> 4750; but 2, 3, 4, 9, 27, whose
+// staged bit 3 leaves 64-byte pieces: 5600 -> 5900), so the host stages the
+// exchanges with lb[i] >= 1 where bits 0..4 are the element and lane bits or
+// the exchanged bit is 3 or above, and leaves the rest to the shuffles.
 __device__ __forceinline__ void staging_slots(const TcXParam &p, int warp, int lane, uint32_t stride,
                                               uint32_t wdst[4], uint32_t rdst[4]) {
 #pragma unroll
@@ -141,7 +148,8 @@ __device__ __forceinline__ void staging_slots(const TcXParam &p, int warp, int l
     int rl = c, sw = 0;
 #pragma unroll
     for (int i = 0; i < 2; i++) {
-      if (!p.stage_xch || i >= p.nswb) break;
+      if (i >= p.nswb) break;
+      if (!((p.stage_xch >> i) & 1)) continue;
       const int lb = p.lb[i];
       rl = (rl & ~(1 << i)) | (((lane >> lb) & 1) << i);
       sw |= ((c >> i) & 1) << lb;
@@ -258,8 +266,8 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
       base = u ? sbase1 : sbase0;
       valid = u ? svalid1 : svalid0;
     }
-    if (p.stage_xch) xch.element<NV>(v);
-    else xch.run<NV>(v);
+    xch.element<NV>(v);
+    xch.lanes<NV>(v, p.stage_xch);
     // row max and squared norm in four independent chains
     float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -551,12 +559,9 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
       for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)(q & ~3) * NT * 16u + rdst[q & 3]);
-      if (p.stage_xch) {
-        xch.element<NV>(v);
-        __syncwarp();  // every lane of the warp has read its slots
-      } else {
-        xch.run<NV>(v);
-      }
+      xch.element<NV>(v);
+      xch.lanes<NV>(v, p.stage_xch);
+      if (p.stage_xch) __syncwarp();  // every lane of the warp has read its slots
       // refill the area with tile t + 2 G
       stage_in(t + 2 * G, u);
       // row max and squared norm in four independent chains
@@ -664,10 +669,16 @@ void fill_xparam(int K, int n, const Block &b, const TcXLayout &x, TcXParam &p) 
   for (int j = 0; j < (K == 6 ? 4 : K - 1); j++) p.rbit[j] = x.rbit[j];
   p.la = x.la;
   p.nswb = x.nswb;
-  p.stage_xch = x.nswb > 0;
+  // staged exchanges (see staging_slots): those with lb[i] >= 1, where a
+  // load's runs cover 256 bytes (bits 0..4 on the element and lane bits) or
+  // the exchanged bit is 3 or above (the staged pieces stay >= 64 bytes)
+  uint64_t eml = 1;
+  for (int i = 0; i < 5; i++) eml |= 1ull << x.lbit[i];
+  const bool long_runs = (eml & 0x1Full) == 0x1Full;
+  p.stage_xch = 0;
   for (int i = 0; i < x.nswb; i++) {
     p.lb[i] = x.lb[i];
-    if (x.lb[i] < 1) p.stage_xch = 0;  // lane bit 0 takes part: shuffles (see staging_slots)
+    if (x.lb[i] >= 1 && (long_runs || x.lbit[x.lb[i]] >= 3)) p.stage_xch |= 1 << i;
   }
   p.part_bit[0] = x.part_bit[0];
   p.part_bit[1] = x.part_bit[1];

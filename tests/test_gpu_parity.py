@@ -290,13 +290,16 @@ def test_tc_lane_exchange(n, k, ctrl, mode, max_ctas):
         assert 2 in kinds
     if k == 5 and ctrl is None:
         # both ways of doing the lane/register exchanges run above: in the
-        # staging copies (every exchanged lane bit >= 1) and by shuffles
-        lbs = []
+        # staging copies (exchanged lane bit >= 1, and bits 0..4 on the
+        # element and lane bits or the exchanged bit >= 3) and by shuffles
+        staged = []
         for pattern in patterns:
             x = qs.qs_tc_exchange_layout(n, pattern)
             if x.applies and x.nswb:
-                lbs.append(min(int(x.lb[i]) for i in range(x.nswb)))
-        assert any(b >= 1 for b in lbs) and any(b == 0 for b in lbs), lbs
+                lanes = [int(b) for b in x.lane_bits]
+                long_runs = {1, 2, 3, 4} <= set(lanes)
+                staged += [int(x.lb[i]) >= 1 and (long_runs or lanes[int(x.lb[i])] >= 3) for i in range(x.nswb)]
+        assert any(staged) and not all(staged), staged
 
 
 @pytest.mark.parametrize("shuffles", [0, 1])
