@@ -8,6 +8,7 @@
 // in the same "slot" order (tc16_build_b). The host layout (which bits sit on
 // lanes and registers, which exchanges run) is tc_exchange_layout below; the
 // planner picks these kernels where tc_exchange_pays.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <type_traits>
@@ -159,7 +160,9 @@ __device__ __forceinline__ void staging_slots(const TcXParam &p, int warp, int l
   }
 }
 
-template <int K>
+// STAGED: some lane/register exchanges are done by the staging copies
+// (p.stage_xch != 0); the other instantiation keeps plain per-thread slots
+template <int K, bool STAGED>
 __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     k_dense_tc16x(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                   int *__restrict__ err) {
@@ -220,8 +223,14 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     return o;
   };
   const LaneExchange xch(p, lane);
-  uint32_t wdst[4], rdst[4];
-  staging_slots(p, warp, lane, kTcThreads * 16u, wdst, rdst);
+  uint32_t wdst[4] = {0, 0, 0, 0}, rdst[4] = {0, 0, 0, 0};
+  if constexpr (STAGED) staging_slots(p, warp, lane, kTcThreads * 16u, wdst, rdst);
+  auto wslot = [&](int r) {
+    return STAGED ? (uint32_t)(r & ~3) * kTcThreads * 16u + wdst[r & 3] : ((uint32_t)r * kTcThreads + (uint32_t)tid) * 16u;
+  };
+  auto rslot = [&](int r) {
+    return STAGED ? (uint32_t)(r & ~3) * kTcThreads * 16u + rdst[r & 3] : ((uint32_t)r * kTcThreads + (uint32_t)tid) * 16u;
+  };
 
   uint32_t phase = 0;
   bool aborted = false;
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
       const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
       for (int r = 0; r < NV; r++)
-        cp_async16(dst + (uint32_t)(r & ~3) * kTcThreads * 16u + wdst[r & 3], a + b + offset(r));
+        cp_async16(dst + wslot(r), a + b + offset(r));
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
@@ -257,17 +266,20 @@ __global__ void __launch_bounds__(kTcThreads, tc16x_occ<K>())
     {
       // this tile's group has landed once at most the next one is pending
       asm volatile("cp.async.wait_group 1;" ::: "memory");
-      if (p.stage_xch) __syncwarp();
+      if constexpr (STAGED) __syncwarp();
       const int u = it & 1;
       const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-      for (int r = 0; r < NV; r++)
-        v[r] = *reinterpret_cast<const float4 *>(src + (uint32_t)(r & ~3) * kTcThreads * 16u + rdst[r & 3]);
+      for (int r = 0; r < NV; r++) v[r] = *reinterpret_cast<const float4 *>(src + rslot(r));
       base = u ? sbase1 : sbase0;
       valid = u ? svalid1 : svalid0;
     }
-    xch.element<NV>(v);
-    xch.lanes<NV>(v, p.stage_xch);
+    if constexpr (STAGED) {
+      xch.element<NV>(v);
+      xch.lanes<NV>(v, p.stage_xch);
+    } else {
+      xch.run<NV>(v);
+    }
     // row max and squared norm in four independent chains
     float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -427,6 +439,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
 }
 }  // namespace x6
 
+// STAGED as in k_dense_tc16x (the unstaged instantiation measured 5% faster
+// than one kernel addressing its slots at run time, for layouts without
+// staged exchanges)
+template <bool STAGED>
 __global__ void __launch_bounds__(x6::kThreads, 1)
     k_dense_tc16x6(float2 *__restrict__ a, const uint4 *__restrict__ bmat, const __grid_constant__ TcXParam p,
                    int *__restrict__ err) {
@@ -535,8 +551,14 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
       return insert_zeros((uint64_t)(t * 4 + (warp & 3)), p.fixed, p.nf) | p.cmask;
     };
     const LaneExchange xch(p, lane);
-    uint32_t wdst[4], rdst[4];
-    staging_slots(p, warp, lane, NT * 16u, wdst, rdst);
+    uint32_t wdst[4] = {0, 0, 0, 0}, rdst[4] = {0, 0, 0, 0};
+    if constexpr (STAGED) staging_slots(p, warp, lane, NT * 16u, wdst, rdst);
+    auto wslot = [&](int q) {
+      return STAGED ? (uint32_t)(q & ~3) * NT * 16u + wdst[q & 3] : ((uint32_t)q * NT + (uint32_t)tid) * 16u;
+    };
+    auto rslot = [&](int q) {
+      return STAGED ? (uint32_t)(q & ~3) * NT * 16u + rdst[q & 3] : ((uint32_t)q * NT + (uint32_t)tid) * 16u;
+    };
 
     // tile t into staging area u: this thread's 16 chunks, one commit group
     // per tile (empty past the last tile, so the group count stays uniform)
@@ -545,7 +567,7 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
         const uint64_t b = tile_base(t);
         const uint32_t dst = smem_addr(sStage) + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-        for (int q = 0; q < NV; q++) cp_async16(dst + (uint32_t)(q & ~3) * NT * 16u + wdst[q & 3], a + b + offset(q));
+        for (int q = 0; q < NV; q++) cp_async16(dst + wslot(q), a + b + offset(q));
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     };
@@ -554,14 +576,18 @@ __global__ void __launch_bounds__(x6::kThreads, 1)
     // input norm (both halves) goes to nin_row[u]; then arrives on ready[u]
     auto convert = [&](long long t, int u) {
       asm volatile("cp.async.wait_group 1;" ::: "memory");
-      if (p.stage_xch) __syncwarp();
+      if constexpr (STAGED) __syncwarp();
       float4 v[NV];
       const unsigned char *src = sStage + (uint32_t)u * STAGE_BYTES;
 #pragma unroll
-      for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + (uint32_t)(q & ~3) * NT * 16u + rdst[q & 3]);
-      xch.element<NV>(v);
-      xch.lanes<NV>(v, p.stage_xch);
-      if (p.stage_xch) __syncwarp();  // every lane of the warp has read its slots
+      for (int q = 0; q < NV; q++) v[q] = *reinterpret_cast<const float4 *>(src + rslot(q));
+      if constexpr (STAGED) {
+        xch.element<NV>(v);
+        xch.lanes<NV>(v, p.stage_xch);
+        __syncwarp();  // every lane of the warp has read its slots
+      } else {
+        xch.run<NV>(v);
+      }
       // refill the area with tile t + 2 G
       stage_in(t + 2 * G, u);
       // row max and squared norm in four independent chains
@@ -697,9 +723,12 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int occ = resident_ctas((const void *)k_dense_tc16x<K>, kTcThreads, smem);
+    int occ = 1 << 30;
+    for (const void *f : {(const void *)k_dense_tc16x<K, false>, (const void *)k_dense_tc16x<K, true>}) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      occ = std::min(occ, resident_ctas(f, kTcThreads, smem));
+    }
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int tmem_cap = 512 / (4 << K);
     per_sm = occ > tc16x_occ<K>() ? tc16x_occ<K>() : occ;
@@ -711,7 +740,8 @@ cudaError_t run_tc16x(float2 *a, int n, const Block &b, const TcXLayout &x, cons
     shape->tiles = p.n_tiles;
     shape->ctas = grid;
   }
-  k_dense_tc16x<K><<<grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  if (p.stage_xch) k_dense_tc16x<K, true><<<grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  else k_dense_tc16x<K, false><<<grid, kTcThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
@@ -725,9 +755,11 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_tc16x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    if (resident_ctas((const void *)k_dense_tc16x6, x6::kThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    for (const void *f : {(const void *)k_dense_tc16x6<false>, (const void *)k_dense_tc16x6<true>}) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      if (resident_ctas(f, x6::kThreads, smem) < 1) return cudaErrorInvalidConfiguration;
+    }
     configured = dev;
   }
   const int grid = tc_grid((long long)dev_info().sms, p.n_tiles, b.tc_max_ctas);  // one CTA per SM
@@ -735,7 +767,8 @@ cudaError_t run_tc16x6(float2 *a, int n, const Block &b, const TcXLayout &x, con
     shape->tiles = p.n_tiles;
     shape->ctas = grid;
   }
-  k_dense_tc16x6<<<grid, x6::kThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  if (p.stage_xch) k_dense_tc16x6<true><<<grid, x6::kThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
+  else k_dense_tc16x6<false><<<grid, x6::kThreads, smem, s>>>(a, (const uint4 *)dev_b, p, err);
   return cudaGetLastError();
 }
 
