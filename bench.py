@@ -355,8 +355,8 @@ def run_ours(args):
 # SHA-256 prefix of the source file the captured kernel was built from: once
 # that file changes the capture no longer describes the kernel and the
 # traffic is reported as null.
-TRAFFIC_PER_LAUNCH = {"k_dense_k5_tcx": (16.21e9, "tc16x.cu", "e3e251e448c08569"),
-                      "k_dense_k6_tcx": (16.20e9, "tc16x.cu", "e3e251e448c08569"),
+TRAFFIC_PER_LAUNCH = {"k_dense_k5_tcx": (16.20e9, "tc16x.cu", "f9754330e219ff77"),
+                      "k_dense_k6_tcx": (16.20e9, "tc16x.cu", "f9754330e219ff77"),
                       "k_dense_k4_tc": (16.21e9, "tc16.cu", "b29b93daaa8320e5")}
 
 
